@@ -1,0 +1,238 @@
+"""FP64 CPU oracle for the GRAPHIC ADI hot path (arXiv:1510.04331).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product package.  The
+arithmetic lives in ``graphic_oracle.c`` (plain C, hand-written radix-2 FFT,
+FP64 throughout, OpenMP over frames / pixels); this module only compiles it
+with gcc and marshals numpy arrays through ctypes.
+
+Functions and the passages they follow:
+
+* ``fft`` / ``dft`` -- Sect. 3.3.1, definition of the Fourier transform.
+* ``shift`` -- Sect. 3.3.1, shift theorem with the separable 2-D phasor on a
+  zero-padded (2x) frame.
+* ``rotate`` -- Sect. 3.4, rotation as three shears, each a 1-D Fourier shift
+  per line on the 2x padded frame.
+* ``alpha_min_deg`` / ``gate_mask`` / ``adi_subtract`` -- Sect. 3.3, the
+  reference-frame condition on field rotation and the per-frame median PSF
+  built without combination coefficients.
+* ``collapse_median`` -- Sect. 3.4, merge of the derotated frames (a median).
+* ``reduce`` -- the four steps chained (Sect. 3, items 3 and 4 of the
+  reduction procedure).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphic_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = ctypes.POINTER(ctypes.c_double)
+_f = ctypes.POINTER(ctypes.c_float)
+_ll = ctypes.POINTER(ctypes.c_longlong)
+_u8 = ctypes.POINTER(ctypes.c_ubyte)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``graphic_oracle.c`` into ``liboracle.so`` next to it (gcc)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.oracle_fft.argtypes = [_d, ctypes.c_int, ctypes.c_int]
+            lib.oracle_dft.argtypes = [_d, _d, ctypes.c_int, ctypes.c_int]
+            lib.oracle_shift_line.argtypes = [_d, _d, ctypes.c_int, ctypes.c_double]
+            lib.oracle_shift.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, _d]
+            lib.oracle_shift_padded.argtypes = [_d, _d, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            lib.oracle_rotate.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, ctypes.c_int]
+            lib.oracle_alpha_min_deg.argtypes = [ctypes.c_double] * 3
+            lib.oracle_alpha_min_deg.restype = ctypes.c_double
+            lib.oracle_gate_mask.argtypes = [_d, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_double, _u8]
+            lib.oracle_annulus_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_int]
+            lib.oracle_adi_subtract_pixels.argtypes = [
+                _d, ctypes.c_longlong, ctypes.c_int, _d, ctypes.c_double, ctypes.c_double, _d, ctypes.c_int,
+                _ll, ctypes.c_longlong, _d]
+            lib.oracle_adi_subtract_pixels_f32.argtypes = [
+                _f, ctypes.c_longlong, ctypes.c_int, _d, ctypes.c_double, ctypes.c_double, _d, ctypes.c_int,
+                _ll, ctypes.c_longlong, _f]
+            lib.oracle_collapse_median_pixels.argtypes = [_d, ctypes.c_longlong, ctypes.c_int, _ll,
+                                                          ctypes.c_longlong, _d]
+            lib.oracle_collapse_median_pixels_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, _ll,
+                                                              ctypes.c_longlong, _f]
+            lib.oracle_reduce.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, _d, _d, ctypes.c_double,
+                                          ctypes.c_double, _d, ctypes.c_int, _d]
+            lib.oracle_last_max_imag.restype = ctypes.c_double
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a, typ):
+    return a.ctypes.data_as(typ)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def last_max_imag() -> float:
+    """Largest |imag part| discarded by the last shift / rotate call."""
+    return _load().oracle_last_max_imag()
+
+
+def fft(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Radix-2 FFT of a complex vector (power-of-two length)."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.complex128)).copy()
+    buf = a.view(np.float64)
+    if _load().oracle_fft(_p(buf, _d), a.size, int(inverse)) != 0:
+        raise ValueError("length must be a power of two")
+    return a
+
+
+def dft(x: np.ndarray, inverse: bool = False) -> np.ndarray:
+    """Brute-force DFT (any length)."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+    out = np.empty_like(a)
+    _load().oracle_dft(_p(a.view(np.float64), _d), _p(out.view(np.float64), _d), a.size, int(inverse))
+    return out
+
+
+def shift_line(x: np.ndarray, d: float) -> np.ndarray:
+    """Periodic Fourier shift of one real line by d (content moves by +d)."""
+    a = _c64(x)
+    out = np.empty_like(a)
+    if _load().oracle_shift_line(_p(a, _d), _p(out, _d), a.size, float(d)) != 0:
+        raise ValueError("length must be a power of two")
+    return out
+
+
+def shift(cube: np.ndarray, dx, dy) -> np.ndarray:
+    """Shift every frame of a [T][N][N] cube by (dx[t], dy[t]) pixels."""
+    c = _c64(cube)
+    T, N, _ = c.shape
+    dx = _c64(np.broadcast_to(dx, (T,)))
+    dy = _c64(np.broadcast_to(dy, (T,)))
+    out = np.empty_like(c)
+    if _load().oracle_shift(_p(c, _d), _p(out, _d), T, N, _p(dx, _d), _p(dy, _d)) != 0:
+        raise ValueError("bad shape")
+    return out
+
+
+def shift_padded(frame: np.ndarray, dx: float, dy: float) -> np.ndarray:
+    """Shift of one N x N frame without the final crop (M x M output)."""
+    f = _c64(frame)
+    N = f.shape[0]
+    out = np.empty((2 * N, 2 * N), np.float64)
+    _load().oracle_shift_padded(_p(f, _d), _p(out, _d), N, float(dx), float(dy))
+    return out
+
+
+def rotate(cube: np.ndarray, theta_deg, reduce90: bool = True) -> np.ndarray:
+    """Rotate every frame of a [T][N][N] cube by theta_deg[t] (CCW)."""
+    c = _c64(cube)
+    T, N, _ = c.shape
+    th = _c64(np.broadcast_to(theta_deg, (T,)))
+    out = np.empty_like(c)
+    if _load().oracle_rotate(_p(c, _d), _p(out, _d), T, N, _p(th, _d), int(reduce90)) != 0:
+        raise ValueError("bad shape")
+    return out
+
+
+def alpha_min_deg(fwhm: float, n_fwhm: float, r: float) -> float:
+    return _load().oracle_alpha_min_deg(float(fwhm), float(n_fwhm), float(r))
+
+
+def gate_mask(parang, i: int, amin_deg: float) -> np.ndarray:
+    pa = _c64(parang)
+    mask = np.zeros(pa.size, np.uint8)
+    _load().oracle_gate_mask(_p(pa, _d), pa.size, int(i), float(amin_deg), _p(mask, _u8))
+    return mask.astype(bool)
+
+
+def annulus_of(i: int, j: int, N: int, edges) -> int:
+    e = _c64(edges)
+    return _load().oracle_annulus_of(int(i), int(j), int(N), _p(e, _d), e.size)
+
+
+def adi_subtract(cube: np.ndarray, parang, fwhm: float, n_fwhm: float, edges, pixels=None) -> np.ndarray:
+    """Angle-gated median PSF subtraction.
+
+    FP64 for float64 cubes, FP32 median arithmetic for float32 cubes.  With
+    ``pixels`` (flat indices) returns an array [n_pix][T]; without, the full
+    residual cube [T][N][N].
+    """
+    f32 = np.asarray(cube).dtype == np.float32
+    c = np.ascontiguousarray(cube, dtype=np.float32 if f32 else np.float64)
+    T, N, _ = c.shape
+    pa = _c64(parang)
+    e = _c64(edges)
+    full = pixels is None
+    pix = np.arange(N * N, dtype=np.int64) if full else np.ascontiguousarray(pixels, dtype=np.int64)
+    out = np.empty((pix.size, T), np.float32 if f32 else np.float64)
+    lib = _load()
+    if f32:
+        rc = lib.oracle_adi_subtract_pixels_f32(_p(c, _f), T, N, _p(pa, _d), float(fwhm), float(n_fwhm),
+                                                _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _f))
+    else:
+        rc = lib.oracle_adi_subtract_pixels(_p(c, _d), T, N, _p(pa, _d), float(fwhm), float(n_fwhm),
+                                            _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _d))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    if full:
+        return np.ascontiguousarray(out.T.reshape(T, N, N))
+    return out
+
+
+def collapse_median(cube: np.ndarray, pixels=None) -> np.ndarray:
+    """Per-pixel median over the frames (FP64, or FP32 for float32 input)."""
+    f32 = np.asarray(cube).dtype == np.float32
+    c = np.ascontiguousarray(cube, dtype=np.float32 if f32 else np.float64)
+    T, N, _ = c.shape
+    full = pixels is None
+    pix = np.arange(N * N, dtype=np.int64) if full else np.ascontiguousarray(pixels, dtype=np.int64)
+    out = np.empty(pix.size, np.float32 if f32 else np.float64)
+    lib = _load()
+    if f32:
+        lib.oracle_collapse_median_pixels_f32(_p(c, _f), T, N, _p(pix, _ll), pix.size, _p(out, _f))
+    else:
+        lib.oracle_collapse_median_pixels(_p(c, _d), T, N, _p(pix, _ll), pix.size, _p(out, _d))
+    return out.reshape(N, N) if full else out
+
+
+def reduce(cube: np.ndarray, dx, dy, parang, fwhm: float, n_fwhm: float, edges) -> np.ndarray:
+    """Shift, median PSF subtraction, derotation by -parang, median collapse."""
+    c = _c64(cube)
+    T, N, _ = c.shape
+    work = np.empty_like(c)
+    out = np.empty((N, N), np.float64)
+    dx = _c64(np.broadcast_to(dx, (T,)))
+    dy = _c64(np.broadcast_to(dy, (T,)))
+    pa = _c64(parang)
+    e = _c64(edges)
+    rc = _load().oracle_reduce(_p(c, _d), _p(work, _d), T, N, _p(dx, _d), _p(dy, _d), _p(pa, _d), float(fwhm),
+                               float(n_fwhm), _p(e, _d), e.size, _p(out, _d))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return out

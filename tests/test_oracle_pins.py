@@ -1,0 +1,372 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: every expected value comes
+from a different route (a library routine, a closed form, an exact index
+map, an invariant, a geometric identity), chosen so that a dropped term,
+a flipped sign, a wrong index or a transposed operand in the oracle fails
+at least one test.  CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_04331_gb300 import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_cases.json")))
+
+
+# --------------------------------------------------------------------------
+# FFT (Sect. 3.3.1 definitions)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [1, 2, 4, 8, 16, 32, 64])
+def test_fft_matches_bruteforce_dft(M):
+    rng = np.random.default_rng(M)
+    x = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    X = oracle.fft(x)
+    D = oracle.dft(x)
+    assert np.abs(X - D).max() <= 1e-13 * max(1.0, np.abs(D).max())
+    # library routine (numpy) as an independent second route
+    assert np.abs(X - np.fft.fft(x)).max() <= 1e-13 * max(1.0, np.abs(D).max())
+    assert np.abs(oracle.fft(x, inverse=True) - np.fft.ifft(x)).max() <= 1e-14 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("M", [128, 1024])
+def test_fft_roundtrip_and_parseval(M):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    X = oracle.fft(x)
+    assert abs(np.sum(np.abs(X) ** 2) / M - np.sum(np.abs(x) ** 2)) <= 1e-11 * np.sum(np.abs(x) ** 2)
+    assert np.abs(oracle.fft(X, inverse=True) - x).max() <= 1e-13
+    # a single tone lands in exactly one bin, at +k for exp(+i 2 pi k n / M)
+    k = 5
+    tone = np.exp(2j * np.pi * k * np.arange(M) / M)
+    T = oracle.fft(tone)
+    assert abs(T[k] - M) < 1e-9 and np.abs(np.delete(T, k)).max() < 1e-9
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        oracle.fft(np.ones(12))
+
+
+# --------------------------------------------------------------------------
+# Shift (Sect. 3.3.1)
+# --------------------------------------------------------------------------
+
+def _roll_zero(f, dx, dy):
+    """out[i][j] = in[i - dy][j - dx], zero where the source is outside."""
+    N = f.shape[-1]
+    out = np.zeros_like(f)
+    for i in range(N):
+        for j in range(N):
+            si, sj = i - dy, j - dx
+            if 0 <= si < N and 0 <= sj < N:
+                out[..., i, j] = f[..., si, sj]
+    return out
+
+
+@pytest.mark.parametrize("dx,dy", [(1, 0), (0, 1), (2, -3), (-4, 4), (8, 8), (-8, -8), (0, 0)])
+def test_integer_shift_is_zero_filled_roll(dx, dy):
+    f = synth.random_frames(1, 16, seed=3).astype(np.float64)
+    out = oracle.shift(f, [dx], [dy])
+    assert np.abs(out - _roll_zero(f, dx, dy)).max() <= 1e-13
+    assert oracle.last_max_imag() <= 1e-13
+
+
+def _dirichlet_line(M, p0, d):
+    """Closed form of a unit impulse at p0 shifted by d on a periodic line of
+    length M with the Nyquist bin weighted by cos(pi d): the Dirichlet kernel
+    sin((K + 1/2) u) / sin(u / 2), K = M/2 - 1, u = 2 pi (n - p0 - d) / M,
+    plus cos(pi d) (-1)^(n - p0), all over M."""
+    n = np.arange(M)
+    u = 2.0 * np.pi * (n - p0 - d) / M
+    K = M // 2 - 1
+    with np.errstate(invalid="ignore", divide="ignore"):
+        core = np.sin((K + 0.5) * u) / np.sin(u / 2.0)
+    core = np.where(np.abs(np.sin(u / 2.0)) < 1e-300, 2 * K + 1.0, core)
+    return (core + np.cos(np.pi * d) * (-1.0) ** (n - p0)) / M
+
+
+def test_gibbs_single_pixel_matches_dirichlet_closed_form():
+    case = GOLD["gibbs_single_pixel_shift"]
+    dx, dy = case["dx"], case["dy"]
+    N = 32
+    M = 2 * N
+    i0, j0 = 13, 17
+    f = np.zeros((1, N, N))
+    f[0, i0, j0] = 1.0
+    out = oracle.shift(f, [dx], [dy])[0]
+    kx = _dirichlet_line(M, j0 + N // 2, dx)[N // 2:N // 2 + N]
+    ky = _dirichlet_line(M, i0 + N // 2, dy)[N // 2:N // 2 + N]
+    assert np.abs(out - np.outer(ky, kx)).max() <= 1e-14
+    # ringing present (the Gibbs pattern of the figure): negative lobes
+    assert out.min() < -0.01
+
+
+def test_shift_of_sampled_gaussian_is_analytic_gaussian():
+    N = 64
+    c = N / 2
+    s = 2.5
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    g = lambda x0, y0: np.exp(-((xx - x0) ** 2 + (yy - y0) ** 2) / (2 * s * s))
+    out = oracle.shift(g(c, c)[None], [1.37], [-2.61])[0]
+    assert np.abs(out - g(c + 1.37, c - 2.61)).max() <= 1e-10
+
+
+def test_shift_round_trip_paper_case():
+    case = GOLD["shift_round_trip"]
+    N = 64
+    f = synth.random_frames(2, N, seed=5, smooth=True, dtype=np.float64)
+    there = oracle.shift(f, [case["dx"]] * 2, [case["dy"]] * 2)
+    back = oracle.shift(there, [-case["dx"]] * 2, [-case["dy"]] * 2)
+    assert np.abs(back - f).max() <= 1e-9 * np.abs(f).max()
+
+
+def test_shift_separable_equals_2d():
+    f = synth.random_frames(1, 32, seed=9).astype(np.float64)
+    both = oracle.shift(f, [0.37], [-1.21])
+    x_then_y = oracle.shift(oracle.shift(f, [0.37], [0.0]), [0.0], [-1.21])
+    assert np.abs(both - x_then_y).max() <= 1e-12
+
+
+def test_shift_flux_conserved_on_padded_frame():
+    f = synth.random_frames(1, 32, seed=11)[0].astype(np.float64)
+    out = oracle.shift_padded(f, 0.41, -0.77)
+    assert abs(out.sum() - f.sum()) <= 1e-11 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("d", [0.0, 0.25, 0.5, 0.9, 3.3, -2.5])
+def test_shift_line_parseval_with_nyquist_term(d):
+    M = 64
+    x = np.random.default_rng(1).standard_normal(M)
+    y = oracle.shift_line(x, d)
+    nyq = np.sum(x * (-1.0) ** np.arange(M))
+    expect = np.sum(x * x) - math.sin(math.pi * d) ** 2 * nyq * nyq / M
+    assert abs(np.sum(y * y) - expect) <= 1e-11 * np.sum(x * x)
+    assert oracle.last_max_imag() <= 1e-12
+
+
+def test_shift_sign_moves_content_positive():
+    N = 64
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    f = np.exp(-((xx - 20.0) ** 2 + (yy - 30.0) ** 2) / (2 * 3.0 ** 2))[None]
+    out = oracle.shift(f, [0.25], [-0.5])[0]
+    # the centroid moves by (+0.25, -0.5): content moves by +d
+    assert abs((out * xx).sum() / out.sum() - 20.25) < 1e-9
+    assert abs((out * yy).sum() / out.sum() - 29.5) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Rotation (Sect. 3.4)
+# --------------------------------------------------------------------------
+
+def _rot90_map(f, q):
+    """Exact rotation by 90 q degrees about (N/2, N/2), counter-clockwise,
+    built from the geometry: output pixel (x, y) takes input R(-90q)(x, y)."""
+    N = f.shape[-1]
+    c = N // 2
+    out = np.zeros_like(f)
+    ang = -q * math.pi / 2
+    ca, sa = round(math.cos(ang)), round(math.sin(ang))
+    for i in range(N):
+        for j in range(N):
+            x, y = j - c, i - c
+            xs, ys = ca * x - sa * y, sa * x + ca * y
+            si, sj = ys + c, xs + c
+            if 0 <= si < N and 0 <= sj < N:
+                out[..., i, j] = f[..., si, sj]
+    return out
+
+
+@pytest.mark.parametrize("theta,q", [(90.0, 1), (180.0, 2), (270.0, 3), (-90.0, 3), (360.0, 0), (450.0, 1)])
+def test_rotation_multiple_of_90_is_exact_index_map(theta, q):
+    f = synth.random_frames(1, 16, seed=2).astype(np.float64)
+    out = oracle.rotate(f, [theta])
+    assert np.array_equal(out, _rot90_map(f, q))
+
+
+@pytest.mark.parametrize("theta,q", [(90.0, 1), (-90.0, 3)])
+def test_raw_three_shear_at_90_equals_index_map(theta, q):
+    f = synth.random_frames(1, 16, seed=4).astype(np.float64)
+    out = oracle.rotate(f, [theta], reduce90=False)
+    assert np.abs(out - _rot90_map(f, q)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("theta", [11.3, -37.0, 44.9, 1.0])
+def test_shear_matrix_identity(theta):
+    t = math.radians(theta)
+    Sx = np.array([[1.0, -math.tan(t / 2)], [0.0, 1.0]])
+    Sy = np.array([[1.0, 0.0], [math.sin(t), 1.0]])
+    R = np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+    assert np.abs(Sx @ Sy @ Sx - R).max() <= 1e-15
+
+
+@pytest.mark.parametrize("theta", [11.3, -30.0, 44.0, 123.4, -161.0])
+def test_rotated_elliptical_gaussian_is_analytic(theta):
+    N = 64
+    c = N / 2
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    sa, sb, phi0, x0, y0 = 3.0, 2.2, math.radians(20.0), 6.0, -4.0
+
+    def g(rot_deg):
+        r = math.radians(rot_deg)
+        # centre and orientation of the content after a CCW rotation by rot_deg
+        cx = c + x0 * math.cos(r) - y0 * math.sin(r)
+        cy = c + x0 * math.sin(r) + y0 * math.cos(r)
+        p = phi0 + r
+        u = (xx - cx) * math.cos(p) + (yy - cy) * math.sin(p)
+        v = -(xx - cx) * math.sin(p) + (yy - cy) * math.cos(p)
+        return np.exp(-(u * u / (2 * sa * sa) + v * v / (2 * sb * sb)))
+
+    out = oracle.rotate(g(0.0)[None], [theta])[0]
+    assert np.abs(out - g(theta)).max() <= 1e-9
+    assert oracle.last_max_imag() <= 1e-12
+
+
+def test_rotation_round_trip_paper_case():
+    th = GOLD["rotation_round_trip"]["theta_deg"]
+    f = synth.random_frames(2, 64, seed=8, smooth=True, dtype=np.float64)
+    back = oracle.rotate(oracle.rotate(f, [th, th]), [-th, -th])
+    assert np.abs(back - f).max() <= 1e-9 * np.abs(f).max()
+
+
+def test_rotation_composes_and_conserves_flux():
+    f = synth.random_frames(1, 64, seed=12, smooth=True, dtype=np.float64)
+    a = oracle.rotate(oracle.rotate(f, [17.0]), [21.0])
+    b = oracle.rotate(f, [38.0])
+    assert np.abs(a - b).max() <= 1e-8 * np.abs(f).max()
+    assert abs(b.sum() - f.sum()) <= 1e-9 * np.abs(f).sum()
+
+
+def test_rotation_moves_point_counter_clockwise():
+    N = 64
+    c = N // 2
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    f = np.exp(-((xx - (c + 10)) ** 2 + (yy - c) ** 2) / (2 * 2.0 ** 2))[None]
+    out = oracle.rotate(f, [30.0])[0]
+    i, j = np.unravel_index(np.argmax(out), out.shape)
+    # (10, 0) rotated by +30 deg -> (8.66, 5.0): row c + 5, col c + 9 (nearest)
+    assert (i, j) == (c + 5, c + 9)
+
+
+# --------------------------------------------------------------------------
+# Gate and medians (Sect. 3.3)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("r", [4.0, 8.0, 16.0, 100.0])
+def test_alpha_min_is_chord_of_n_fwhm(r):
+    fwhm, n = 4.0, 1.5
+    a = oracle.alpha_min_deg(fwhm, n, r)
+    # two points at radius r, alpha_min apart, are n * FWHM apart (chord)
+    chord = 2.0 * r * math.sin(math.radians(a) / 2.0)
+    if n * fwhm < 2.0 * r:
+        assert abs(chord - n * fwhm) <= 1e-12 * n * fwhm
+    else:
+        assert a == 180.0
+
+
+def test_gate_invariants():
+    rng = np.random.default_rng(3)
+    pa = np.sort(rng.uniform(-30, 30, 40))
+    amin = 7.5
+    masks = [oracle.gate_mask(pa, i, amin) for i in range(40)]
+    for i in range(40):
+        m = masks[i]
+        assert not m[i]
+        if m.any():
+            # exactly the frames rotated by more than alpha_min, both sides
+            d = np.abs(pa - pa[i])
+            assert np.array_equal(m, d > amin)
+            for k in np.nonzero(m)[0]:
+                assert masks[k][i]  # symmetric
+    # a larger alpha_min gives a subset
+    for i in range(40):
+        m2 = oracle.gate_mask(pa, i, amin * 2)
+        if m2.any() and masks[i].any():
+            assert not np.any(m2 & ~masks[i])
+
+
+def test_gate_empty_set_falls_back_to_farthest_frames():
+    pa = np.array([0.0, 1.0, 2.0, 3.0, 4.0])
+    m = oracle.gate_mask(pa, 2, 10.0)     # nothing is 10 deg away
+    assert m.tolist() == [True, False, False, False, True]   # tie: both ends
+    m = oracle.gate_mask(pa, 1, 10.0)
+    assert m.tolist() == [False, False, False, False, True]
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 7, 32, 33])
+def test_collapse_median_f32_matches_numpy_bit_exact(T):
+    rng = np.random.default_rng(T)
+    c = (rng.standard_normal((T, 8, 8)) * 100).astype(np.float32)
+    c[:, 0, 0] = 5.0  # ties
+    ours = oracle.collapse_median(c)
+    assert ours.dtype == np.float32
+    assert np.array_equal(ours, np.median(c, axis=0).astype(np.float32))
+
+
+def test_adi_subtract_small_alpha_min_is_median_of_others():
+    # with fwhm -> 0 the gate keeps every frame with a different angle
+    T, N = 9, 8
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal((T, N, N)).astype(np.float32)
+    pa = np.linspace(0, 40, T)
+    edges = [0.5, 100.0]          # every pixel but the centre one (rho = 0)
+    res = oracle.adi_subtract(c, pa, 1e-9, 1.0, edges)
+    for t in range(T):
+        others = np.delete(c, t, axis=0)
+        expect = (c[t] - np.median(others, axis=0)).astype(np.float32)
+        expect[N // 2, N // 2] = 0.0
+        assert np.array_equal(res[t], expect)
+
+
+def test_adi_subtract_masks_pixels_outside_annuli_and_uses_farthest_when_empty():
+    T, N = 5, 16
+    rng = np.random.default_rng(6)
+    c = rng.standard_normal((T, N, N))
+    pa = np.array([0.0, 1.0, 2.0, 3.0, 4.0])
+    edges = [2.0, 5.0]
+    res = oracle.adi_subtract(c, pa, 4.0, 1.5, edges)   # alpha_min > 4 deg -> fallback
+    for i in range(N):
+        for j in range(N):
+            rho2 = (i - N // 2) ** 2 + (j - N // 2) ** 2
+            if not (4.0 <= rho2 < 25.0):
+                assert np.all(res[:, i, j] == 0.0)
+            else:
+                assert res[0, i, j] == c[0, i, j] - c[4, i, j]
+                assert res[2, i, j] == c[2, i, j] - 0.5 * (c[0, i, j] + c[4, i, j])
+
+
+# --------------------------------------------------------------------------
+# Whole reduction
+# --------------------------------------------------------------------------
+
+def test_reduce_recovers_companion_at_injected_position():
+    # noise-free small workload: the companion must come back at its
+    # injected (r, PA0) once the frames are recentred, PSF-subtracted and
+    # derotated by -parang (centroid within 0.5 px, as the registration
+    # accuracy the paper quotes in Sect. 3.1)
+    d = synth.make_cube(32, 128, 0, parang=np.linspace(0.0, 40.0, 32), peak=1e4, noise=False)
+    out = oracle.reduce(d.cube, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges)
+    c = 128 // 2
+    for (r, pa0, con) in d.companions:
+        x = c + r * math.cos(math.radians(pa0))
+        y = c + r * math.sin(math.radians(pa0))
+        i0, j0 = int(round(y)), int(round(x))
+        win = np.clip(out[i0 - 2:i0 + 3, j0 - 2:j0 + 3], 0, None)
+        ii, jj = np.mgrid[i0 - 2:i0 + 3, j0 - 2:j0 + 3]
+        assert abs((win * ii).sum() / win.sum() - y) <= 0.5
+        assert abs((win * jj).sum() / win.sum() - x) <= 0.5
+        assert out[i0, j0] > 0.3 * 1e4 * con
+
+
+def test_reduce_of_static_cube_is_zero():
+    T, N = 6, 16
+    f = synth.random_frames(1, N, seed=1).astype(np.float64)
+    c = np.repeat(f, T, axis=0)
+    out = oracle.reduce(c, np.zeros(T), np.zeros(T), np.linspace(0, 50, T), 4.0, 1.0, [0.0, 12.0])
+    assert np.abs(out).max() <= 1e-12
