@@ -1,0 +1,175 @@
+/*
+ * graphic.h -- C ABI of the GB300 (sm_103a) library for the data-parallel
+ * hot path of the GRAPHIC angular-differential-imaging reduction
+ * (Hugelier et al., arXiv:1510.04331): Fourier recentring shift, angle-gated
+ * median PSF subtraction, Fourier three-shear derotation, median collapse.
+ *
+ * General rules for every call below:
+ *   - Cubes are FP32, C-contiguous [n_frames][n][n] (frame-major, row-major
+ *     frames) in DEVICE memory owned by the caller, except in the *_host
+ *     calls, whose cube and result pointers are HOST memory.  n is a power
+ *     of two in [64, 1024]; the frame centre is pixel (row n/2, col n/2).
+ *   - Per-frame parameter arrays (dx, dy, theta, parang) are HOST arrays of
+ *     n_frames doubles, owned by the caller, read before the call returns.
+ *   - n_frames == 0 is a no-op for graphic_shift and graphic_rotate (the
+ *     pointers may then be NULL); the median calls need n_frames >= 1.
+ *   - Calls are enqueued on the context's stream (graphic_set_stream; the
+ *     legacy default stream otherwise) and wait for it before returning, so
+ *     the returned status covers the device work.  in and out may be the
+ *     same pointer (in place); partially overlapping buffers are undefined.
+ *   - Return value: GRAPHIC_OK (0) or a negative GRAPHIC_ERR_* code; a
+ *     message for the last failure of the calling thread is available from
+ *     graphic_last_error().  On error the output contents are unspecified.
+ *   - Inputs must be finite; a NaN or Inf seen on the device gives
+ *     GRAPHIC_ERR_NONFINITE.
+ *   - The library allocates its own device workspaces (plan arrays, the
+ *     scratch of the rotation) on first use and keeps them per context until
+ *     graphic_release() or graphic_destroy().
+ */
+#ifndef GRAPHIC_H
+#define GRAPHIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRAPHIC_OK 0
+#define GRAPHIC_ERR_INVALID_ARG -1   /* null pointer, bad size, bad parameter  */
+#define GRAPHIC_ERR_UNSUPPORTED -2   /* n or n_frames outside what is built    */
+#define GRAPHIC_ERR_OOM -3           /* device allocation failed               */
+#define GRAPHIC_ERR_CUDA -4          /* CUDA runtime error                     */
+#define GRAPHIC_ERR_NONFINITE -5     /* NaN or Inf in the input cube           */
+#define GRAPHIC_ERR_TIMEOUT -6       /* bounded device wait ran out            */
+#define GRAPHIC_ERR_INTERNAL -7      /* device-side consistency check failed   */
+
+/* Largest frame count the median kernels take in one call. */
+#define GRAPHIC_MAX_FRAMES_MEDIAN 2048
+
+typedef struct graphic_ctx graphic_ctx;
+
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ * Fails with GRAPHIC_ERR_UNSUPPORTED if the device is not sm_103. */
+int graphic_create(graphic_ctx **out, int device);
+
+/* Free every device and host resource of the context (waits for its stream). */
+int graphic_destroy(graphic_ctx *ctx);
+
+/* Free the context's workspaces (they are re-created on demand). */
+int graphic_release(graphic_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t, may be NULL for the legacy default stream)
+ * for every later call on this context.  The stream stays owned by the
+ * caller. */
+int graphic_set_stream(graphic_ctx *ctx, void *stream);
+
+/* Message of the last failing call made by the calling thread ("" if none). */
+const char *graphic_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int graphic_version(void);
+
+/*
+ * Sub-pixel recentring shift (Sect. 3.3.1, shift theorem with the separable
+ * 2-D phasor, on frames zero-padded to m = 2n).  Frame t is moved by
+ * (dx[t], dy[t]) pixels: out(x, y) = in(x - dx, y - dy), computed as a row
+ * pass then a column pass, each line padded to m (data at offset n/2),
+ * transformed, multiplied by exp(-i 2 pi k d / m) on signed bins k (the
+ * Nyquist bin by cos(pi d)), transformed back, cropped to the same n
+ * samples.  |dx|, |dy| <= n/2 (GRAPHIC_ERR_INVALID_ARG otherwise).
+ */
+int graphic_shift(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n,
+                  const double *dx, const double *dy);
+
+/*
+ * Fourier three-shear rotation (Sect. 3.4, rotation matrix written as
+ * S_x(-tan(theta/2)) S_y(sin theta) S_x(-tan(theta/2)), each shear a 1-D
+ * Fourier shift per line of the 2x zero-padded frame).  Frame t is rotated
+ * by theta_deg[t] degrees counter-clockwise about pixel (n/2, n/2): content
+ * at (x, y) = (col - n/2, row - n/2) moves to (x cos - y sin, x sin + y cos).
+ * theta = 90 q + theta' with q = floor(theta/90 + 1/2): the 90 q part is an
+ * exact index map (zero where the source pixel is outside the frame), the
+ * shears use theta' in [-45, 45) and are skipped when theta' == 0.
+ * Uses a device scratch of (frames per chunk) * n * 2n floats.
+ */
+int graphic_rotate(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n,
+                   const double *theta_deg);
+
+/*
+ * Angle-gated median PSF subtraction (Sect. 3.3, reference-frame conditions
+ * and a per-frame PSF built as a plain median, without coefficients).
+ * annuli_edges[0] < ... < annuli_edges[n_edges-1] (pixels) define
+ * n_edges - 1 annuli; pixel p (rho^2 = x^2 + y^2) belongs to annulus a when
+ * edges[a]^2 <= rho^2 < edges[a+1]^2 and is set to 0 in every frame when it
+ * belongs to none.  For annulus a, alpha_min = 2 asin(min(1, n_fwhm * fwhm /
+ * (2 edges[a]))) (degrees); frame t's reference set is every frame k with
+ * |parang[k] - parang[t]| > alpha_min, or, when that set is empty, the
+ * frame(s) with the largest |parang[k] - parang[t]|.
+ * out[t](p) = in[t](p) - median over the reference set of in[k](p), the
+ * median taken in the IEEE total order, even counts averaging the two
+ * middle values in FP32.  n_frames <= GRAPHIC_MAX_FRAMES_MEDIAN.
+ */
+int graphic_adi_subtract(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n,
+                         const double *parang_deg, double fwhm, double n_fwhm, const double *annuli_edges,
+                         int32_t n_edges);
+
+/*
+ * Median collapse (Sect. 3.4, merge of the derotated frames): out(p) = median
+ * over the n_frames frames of in[t](p), same median rule as above.  out is a
+ * device buffer of n*n floats.  Any n_frames >= 1.
+ */
+int graphic_collapse_median(graphic_ctx *ctx, const float *in, int64_t n_frames, int32_t n, float *out);
+
+/*
+ * The whole reduction (Sect. 3, PSF subtraction then derotation and merge):
+ * shift by (dx, dy) from `in` into `work`, median PSF subtraction in place in
+ * `work`, derotation by theta = -parang in place in `work`, median collapse
+ * of `work` into `out` (n*n).  `in` is only read; `work` holds n_frames*n*n
+ * floats and may equal `in` (the input is then overwritten).
+ */
+int graphic_reduce(graphic_ctx *ctx, const float *in, float *work, int64_t n_frames, int32_t n,
+                   const double *dx, const double *dy, const double *parang_deg, double fwhm, double n_fwhm,
+                   const double *annuli_edges, int32_t n_edges, float *out);
+
+/*
+ * graphic_reduce with HOST buffers: copies host_in (n_frames*n*n floats) to
+ * a device cube the context owns, reduces it, copies the n*n result back to
+ * host_out.  Pinned (page-locked) host memory gives the fastest copies.
+ */
+int graphic_reduce_host(graphic_ctx *ctx, const float *host_in, int64_t n_frames, int32_t n, const double *dx,
+                        const double *dy, const double *parang_deg, double fwhm, double n_fwhm,
+                        const double *annuli_edges, int32_t n_edges, float *host_out);
+
+/* ---- measurement support ------------------------------------------------ */
+
+/* Kernel identifiers for graphic_profile_read. */
+#define GRAPHIC_K_SHIFT_X 0
+#define GRAPHIC_K_SHIFT_Y 1
+#define GRAPHIC_K_ADI_MEDIAN 2
+#define GRAPHIC_K_ROT_P1 3
+#define GRAPHIC_K_ROT_P2 4
+#define GRAPHIC_K_ROT_P3 5
+#define GRAPHIC_K_COLLAPSE 6
+#define GRAPHIC_K_COUNT 7
+
+/* enable != 0: bracket every kernel launch of the context with CUDA events
+ * on its stream and accumulate per-kernel device time and launch counts;
+ * enable == 0 stops.  Enabling resets the counters. */
+int graphic_profile(graphic_ctx *ctx, int enable);
+
+/* Copy the accumulated device milliseconds and launch counts of the first
+ * n kernels (ids above) into ms[] and launches[] (host arrays of n). */
+int graphic_profile_read(graphic_ctx *ctx, double *ms, int64_t *launches, int32_t n);
+
+/* Name of kernel id `k` (static string), NULL if out of range. */
+const char *graphic_kernel_name(int32_t k);
+
+/* Bytes of device workspace the context currently holds. */
+int graphic_workspace_bytes(graphic_ctx *ctx, int64_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHIC_H */

@@ -1,0 +1,667 @@
+// capi.cu -- C ABI of the GRAPHIC GB300 library (declared in include/graphic.h):
+// argument checks, FP64 host plans, workspaces, kernel orchestration.
+//
+// Host plans (FP64, computed per call):
+//   shift   dx[t], dy[t] uploaded as they are;
+//   rotate  theta = 90 q + theta', q = floor(theta/90 + 1/2) (Sect. 3.4 shears
+//           need |theta'| <= 45 deg to keep tan(theta'/2) bounded), then
+//           a = tan(theta'/2), s = sin(theta') per frame;
+//   adi     frames sorted by parallactic angle (stable), and for every annulus
+//           and sorted position s the reference set {k : |alpha_k - alpha_s|
+//           > alpha_min} (Sect. 3.3) written as sorted-position ranges
+//           [0, L) u [R, T) -- exact, because |fl(alpha_k - alpha_s)| is
+//           monotone on either side of s -- with the farthest-frame fallback
+//           when that set is empty.
+// Work order of graphic_rotate / graphic_shift: frames are processed in
+// chunks sized so that a chunk's intermediate data (the n x 2n scratch of
+// the rotation) stays within the L2 cache between the passes.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/graphic.h"
+#include "graphic_internal.h"
+
+using namespace graphic;
+
+struct graphic_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int *d_status = nullptr;
+  int *h_status = nullptr;          // pinned
+  char *d_plan = nullptr;
+  size_t d_plan_bytes = 0;
+  char *h_plan = nullptr;           // pinned staging
+  size_t h_plan_bytes = 0;
+  float *d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  float *d_cube = nullptr;          // graphic_reduce_host device copy of the input
+  size_t cube_bytes = 0;
+  float *d_img = nullptr;           // graphic_reduce_host device result
+  size_t img_bytes = 0;
+  bool prof = false;
+  double prof_ms[GRAPHIC_K_COUNT] = {};
+  int64_t prof_n[GRAPHIC_K_COUNT] = {};
+  std::vector<cudaEvent_t> ev;      // event pool, pairs
+  std::vector<int> ev_kernel;       // kernel id per used pair
+  size_t ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  return fail(e == cudaErrorMemoryAllocation ? GRAPHIC_ERR_OOM : GRAPHIC_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool supported_n(int32_t n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+
+int check_cube(const void *in, const void *out, int64_t T, int32_t n) {
+  if (T < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 0");
+  if (T > 0 && (!in || !out)) return fail(GRAPHIC_ERR_INVALID_ARG, "null cube pointer");
+  if (!supported_n(n)) return fail(GRAPHIC_ERR_UNSUPPORTED, "n must be one of 64, 128, 256, 512, 1024");
+  return GRAPHIC_OK;
+}
+
+int ensure(void **ptr, size_t *have, size_t need, bool pinned) {
+  if (*have >= need && *ptr) return GRAPHIC_OK;
+  if (*ptr) {
+    if (pinned) cudaFreeHost(*ptr); else cudaFree(*ptr);
+    *ptr = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = pinned ? cudaMallocHost(ptr, need) : cudaMalloc(ptr, need);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_fail(e, pinned ? "cudaMallocHost" : "cudaMalloc");
+  }
+  *have = need;
+  return GRAPHIC_OK;
+}
+
+// --- profiling ------------------------------------------------------------
+void prof_begin(graphic_ctx *c, int k) {
+  if (!c->prof) return;
+  if (c->ev.size() < 2 * (c->ev_used + 1)) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    c->ev.push_back(a);
+    c->ev.push_back(b);
+    c->ev_kernel.push_back(k);
+  }
+  c->ev_kernel[c->ev_used] = k;
+  cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+}
+void prof_end(graphic_ctx *c) {
+  if (!c->prof) return;
+  cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
+  c->ev_used++;
+}
+void prof_collect(graphic_ctx *c) {
+  for (size_t i = 0; i < c->ev_used; i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) {
+      c->prof_ms[c->ev_kernel[i]] += ms;
+      c->prof_n[c->ev_kernel[i]] += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+// --- plan upload ----------------------------------------------------------
+struct PlanBuilder {
+  std::vector<char> buf;
+  size_t add(const void *src, size_t bytes) {
+    size_t off = (buf.size() + 15) & ~size_t(15);
+    buf.resize(off + bytes);
+    if (bytes) memcpy(buf.data() + off, src, bytes);
+    return off;
+  }
+};
+
+int upload_plan(graphic_ctx *c, const PlanBuilder &pb) {
+  const size_t bytes = std::max<size_t>(pb.buf.size(), 16);
+  int rc = ensure((void **)&c->h_plan, &c->h_plan_bytes, bytes, true);
+  if (rc) return rc;
+  rc = ensure((void **)&c->d_plan, &c->d_plan_bytes, bytes, false);
+  if (rc) return rc;
+  memcpy(c->h_plan, pb.buf.data(), pb.buf.size());
+  CK(cudaMemcpyAsync(c->d_plan, c->h_plan, pb.buf.size(), cudaMemcpyHostToDevice, c->stream));
+  return GRAPHIC_OK;
+}
+
+int begin_call(graphic_ctx *c) {
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  return GRAPHIC_OK;
+}
+
+// Wait for the stream, collect profile events, turn the status word into a code.
+int end_call(graphic_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  prof_collect(c);
+  if (*c->h_status & STATUS_NONFINITE) return fail(GRAPHIC_ERR_NONFINITE, "non-finite value in the input cube");
+  if (*c->h_status & STATUS_INTERNAL) return fail(GRAPHIC_ERR_INTERNAL, "device consistency check failed");
+  return GRAPHIC_OK;
+}
+
+long long chunk_frames(int n, long long T, size_t bytes_per_frame) {
+  size_t budget = (size_t)64 << 20;
+  if (const char *e = getenv("GRAPHIC_CHUNK_MB")) {
+    long v = atol(e);
+    if (v > 0) budget = (size_t)v << 20;
+  }
+  long long c = (long long)(budget / bytes_per_frame);
+  if (c < 1) c = 1;
+  if (c > T) c = T;
+  (void)n;
+  return c;
+}
+
+// --- shift ------------------------------------------------------------------
+int validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
+  if (T > 0 && (!dx || !dy)) return fail(GRAPHIC_ERR_INVALID_ARG, "null dx/dy");
+  for (int64_t t = 0; t < T; t++) {
+    if (!isfinite(dx[t]) || !isfinite(dy[t])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite shift");
+    if (fabs(dx[t]) > n / 2 || fabs(dy[t]) > n / 2) return fail(GRAPHIC_ERR_INVALID_ARG, "|shift| > n/2");
+  }
+  return GRAPHIC_OK;
+}
+
+// Enqueue the two shift passes for frames [0, T) with parameters at device
+// pointers p_dx, p_dy.  in -> out (out may equal in).
+int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *p_dx,
+                  const double *p_dy) {
+  const long long NN = (long long)n * n;
+  const long long ch = chunk_frames(n, T, (size_t)NN * sizeof(float));
+  for (long long f0 = 0; f0 < T; f0 += ch) {
+    const long long nf = std::min<long long>(ch, T - f0);
+    LineArgs a{};
+    a.in = in + f0 * NN;
+    a.out = out + f0 * NN;
+    a.p0 = p_dx + f0;
+    a.p1 = p_dy + f0;
+    a.status = c->d_status;
+    a.in_fstride = NN;
+    a.out_fstride = NN;
+    a.n = n;
+    prof_begin(c, GRAPHIC_K_SHIFT_X);
+    cudaError_t e = launch_line_pass(SHIFT_X, a, nf, c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "shift x pass");
+    a.in = out + f0 * NN;
+    prof_begin(c, GRAPHIC_K_SHIFT_Y);
+    e = launch_line_pass(SHIFT_Y, a, nf, c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "shift y pass");
+  }
+  return GRAPHIC_OK;
+}
+
+// --- rotate -----------------------------------------------------------------
+struct RotPlanHost {
+  std::vector<double> a, s;
+  std::vector<int> q;
+};
+
+int plan_rotate(const double *theta, int64_t T, bool negate, RotPlanHost &rp) {
+  rp.a.resize(T);
+  rp.s.resize(T);
+  rp.q.resize(T);
+  for (int64_t t = 0; t < T; t++) {
+    const double th = negate ? -theta[t] : theta[t];
+    if (!isfinite(th) || fabs(th) > 1e6) return fail(GRAPHIC_ERR_INVALID_ARG, "angle not finite or |angle| > 1e6 deg");
+    const int q = (int)floor(th / 90.0 + 0.5);
+    const double tp = th - 90.0 * (double)q;
+    if (tp == 0.0) {
+      rp.a[t] = 0.0;
+      rp.s[t] = 0.0;
+    } else {
+      const double r = tp * kPi / 180.0;
+      rp.a[t] = tan(r / 2.0);
+      rp.s[t] = sin(r);
+    }
+    rp.q[t] = ((q % 4) + 4) % 4;
+  }
+  return GRAPHIC_OK;
+}
+
+int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *p_a,
+                   const double *p_s, const int *p_q) {
+  const long long NN = (long long)n * n;
+  const long long NM = NN * 2;
+  const long long ch = chunk_frames(n, T, (size_t)NM * sizeof(float));
+  int rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, (size_t)ch * NM * sizeof(float), false);
+  if (rc) return rc;
+  for (long long f0 = 0; f0 < T; f0 += ch) {
+    const long long nf = std::min<long long>(ch, T - f0);
+    LineArgs a{};
+    a.p0 = p_a + f0;
+    a.p1 = p_s + f0;
+    a.q = p_q + f0;
+    a.status = c->d_status;
+    a.n = n;
+    // pass 1: frame rows (after rot90^q) -> scratch rows of 2n
+    a.in = in + f0 * NN;
+    a.out = c->d_scratch;
+    a.in_fstride = NN;
+    a.out_fstride = NM;
+    prof_begin(c, GRAPHIC_K_ROT_P1);
+    cudaError_t e = launch_line_pass(ROT_P1, a, nf, c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "rotation pass 1");
+    // pass 2: scratch columns, in place
+    a.in = c->d_scratch;
+    a.out = c->d_scratch;
+    a.in_fstride = NM;
+    a.out_fstride = NM;
+    prof_begin(c, GRAPHIC_K_ROT_P2);
+    e = launch_line_pass(ROT_P2, a, nf, c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "rotation pass 2");
+    // pass 3: scratch rows -> frame rows
+    a.out = out + f0 * NN;
+    a.out_fstride = NN;
+    prof_begin(c, GRAPHIC_K_ROT_P3);
+    e = launch_line_pass(ROT_P3, a, nf, c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "rotation pass 3");
+  }
+  return GRAPHIC_OK;
+}
+
+// --- adi --------------------------------------------------------------------
+int validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+  if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
+  if (T > GRAPHIC_MAX_FRAMES_MEDIAN) return fail(GRAPHIC_ERR_UNSUPPORTED, "n_frames > GRAPHIC_MAX_FRAMES_MEDIAN");
+  if (!parang) return fail(GRAPHIC_ERR_INVALID_ARG, "null parang");
+  if (!edges || n_edges < 2 || n_edges > 4096) return fail(GRAPHIC_ERR_INVALID_ARG, "need 2..4096 annulus edges");
+  if (!(fwhm > 0) || !isfinite(fwhm) || !(n_fwhm > 0) || !isfinite(n_fwhm))
+    return fail(GRAPHIC_ERR_INVALID_ARG, "fwhm and n_fwhm must be finite and > 0");
+  for (int32_t i = 0; i < n_edges; i++) {
+    if (!isfinite(edges[i]) || edges[i] < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "annulus edges must be finite, >= 0");
+    if (i && !(edges[i] > edges[i - 1])) return fail(GRAPHIC_ERR_INVALID_ARG, "annulus edges must increase");
+  }
+  for (int64_t t = 0; t < T; t++)
+    if (!isfinite(parang[t])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite parallactic angle");
+  return GRAPHIC_OK;
+}
+
+struct AdiPlanHost {
+  std::vector<int> perm;
+  std::vector<int> lr;      // [A][T][2]
+  std::vector<double> edge2;
+};
+
+double alpha_min_deg(double fwhm, double n_fwhm, double r) {
+  double arg = n_fwhm * fwhm / (2.0 * r);
+  if (!(arg < 1.0)) arg = 1.0;
+  return 2.0 * asin(arg) * 180.0 / kPi;
+}
+
+void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
+              AdiPlanHost &ap) {
+  const int A = n_edges - 1;
+  ap.perm.resize(T);
+  for (int64_t t = 0; t < T; t++) ap.perm[t] = (int)t;
+  std::stable_sort(ap.perm.begin(), ap.perm.end(), [&](int x, int y) { return parang[x] < parang[y]; });
+  ap.edge2.resize(n_edges);
+  for (int i = 0; i < n_edges; i++) ap.edge2[i] = edges[i] * edges[i];
+  ap.lr.assign((size_t)A * T * 2, 0);
+  std::vector<double> al(T);
+  for (int64_t s = 0; s < T; s++) al[s] = parang[ap.perm[s]];
+  for (int a = 0; a < A; a++) {
+    const double amin = alpha_min_deg(fwhm, n_fwhm, edges[a]);
+    int *lr = ap.lr.data() + (size_t)a * T * 2;
+    for (int64_t s = 0; s < T; s++) {
+      const double ai = al[s];
+      auto pred = [&](int64_t k) { return fabs(al[k] - ai) > amin; };
+      // [0, s]: pred true ... true false ... false
+      int64_t lo = 0, hi = s;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (pred(mid)) lo = mid + 1; else hi = mid;
+      }
+      int64_t L = lo;
+      // [s, T): pred false ... false true ... true
+      lo = s;
+      hi = T;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (pred(mid)) hi = mid; else lo = mid + 1;
+      }
+      int64_t R = lo;
+      if (L == 0 && R == T) {
+        // empty: the frame(s) farthest in angle
+        const double best = std::max(fabs(al[0] - ai), fabs(al[T - 1] - ai));
+        int64_t l2 = 0;
+        while (l2 < T && fabs(al[l2] - ai) == best) l2++;
+        int64_t r2 = T;
+        if (l2 < T)
+          while (r2 > l2 && fabs(al[r2 - 1] - ai) == best) r2--;
+        else
+          r2 = T;
+        L = l2;
+        R = r2;
+      }
+      lr[2 * s] = (int)L;
+      lr[2 * s + 1] = (int)R;
+    }
+  }
+}
+
+int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
+                const int *p_lr, const double *p_edge2, int n_ann) {
+  AdiArgs a{};
+  a.in = in;
+  a.out = out;
+  a.perm = p_perm;
+  a.lr = p_lr;
+  a.edge2 = p_edge2;
+  a.status = c->d_status;
+  a.T = (int)T;
+  a.n = n;
+  a.n_ann = n_ann;
+  prof_begin(c, GRAPHIC_K_ADI_MEDIAN);
+  cudaError_t e = launch_adi_median(a, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "median PSF kernel");
+  return GRAPHIC_OK;
+}
+
+int enqueue_collapse(graphic_ctx *c, const float *in, int64_t T, int32_t n, float *out) {
+  CollapseArgs a{};
+  a.in = in;
+  a.out = out;
+  a.status = c->d_status;
+  a.T = T;
+  a.n = n;
+  prof_begin(c, GRAPHIC_K_COLLAPSE);
+  cudaError_t e = launch_collapse(a, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "collapse kernel");
+  return GRAPHIC_OK;
+}
+
+template <class T>
+const T *at(const graphic_ctx *c, size_t off) {
+  return reinterpret_cast<const T *>(c->d_plan + off);
+}
+
+int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
+                  const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
+                  int32_t n_edges, float *out) {
+  int rc = validate_shift(dx, dy, T, n);
+  if (rc) return rc;
+  rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges);
+  if (rc) return rc;
+  RotPlanHost rp;
+  rc = plan_rotate(parang, T, true, rp);
+  if (rc) return rc;
+  AdiPlanHost ap;
+  plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap);
+  PlanBuilder pb;
+  const size_t o_dx = pb.add(dx, T * sizeof(double));
+  const size_t o_dy = pb.add(dy, T * sizeof(double));
+  const size_t o_a = pb.add(rp.a.data(), T * sizeof(double));
+  const size_t o_s = pb.add(rp.s.data(), T * sizeof(double));
+  const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
+  const size_t o_q = pb.add(rp.q.data(), T * sizeof(int));
+  const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
+  const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
+  if ((rc = enqueue_adi(c, work, work, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
+                        n_edges - 1)))
+    return rc;
+  if ((rc = enqueue_rotate(c, work, work, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q)))) return rc;
+  if ((rc = enqueue_collapse(c, work, T, n, out))) return rc;
+  return GRAPHIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int graphic_version(void) { return 10000; }
+
+const char *graphic_last_error(void) { return g_err.c_str(); }
+
+int graphic_create(graphic_ctx **out, int device) {
+  if (!out) return fail(GRAPHIC_ERR_INVALID_ARG, "null out");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(GRAPHIC_ERR_INVALID_ARG, "no such device");
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(GRAPHIC_ERR_UNSUPPORTED, "built for sm_103a (GB300); device is sm_" + std::to_string(prop.major) +
+                                             std::to_string(prop.minor));
+  DeviceGuard g(device);
+  graphic_ctx *c = new graphic_ctx();
+  c->device = device;
+  if (geom_init_device() != 0) {
+    delete c;
+    return fail(GRAPHIC_ERR_CUDA, "twiddle table upload failed");
+  }
+  e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, sizeof(int));
+  if (e != cudaSuccess) {
+    graphic_destroy(c);
+    return cuda_fail(e, "context allocation");
+  }
+  *out = c;
+  return GRAPHIC_OK;
+}
+
+int graphic_release(graphic_ctx *c) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_plan);
+  cudaFreeHost(c->h_plan);
+  cudaFree(c->d_scratch);
+  cudaFree(c->d_cube);
+  cudaFree(c->d_img);
+  c->d_plan = nullptr;
+  c->h_plan = nullptr;
+  c->d_scratch = nullptr;
+  c->d_cube = nullptr;
+  c->d_img = nullptr;
+  c->d_plan_bytes = c->h_plan_bytes = c->scratch_bytes = c->cube_bytes = c->img_bytes = 0;
+  return GRAPHIC_OK;
+}
+
+int graphic_destroy(graphic_ctx *c) {
+  if (!c) return GRAPHIC_OK;
+  graphic_release(c);
+  DeviceGuard g(c->device);
+  cudaFree(c->d_status);
+  cudaFreeHost(c->h_status);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+  return GRAPHIC_OK;
+}
+
+int graphic_set_stream(graphic_ctx *c, void *stream) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  c->stream = (cudaStream_t)stream;
+  return GRAPHIC_OK;
+}
+
+int graphic_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *dx,
+                  const double *dy) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if ((rc = validate_shift(dx, dy, T, n))) return rc;
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_dx = pb.add(dx, T * sizeof(double));
+  const size_t o_dy = pb.add(dy, T * sizeof(double));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_shift(c, in, out, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
+  return end_call(c);
+}
+
+int graphic_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *theta) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if (T > 0 && !theta) return fail(GRAPHIC_ERR_INVALID_ARG, "null theta");
+  if (T == 0) return GRAPHIC_OK;
+  RotPlanHost rp;
+  if ((rc = plan_rotate(theta, T, false, rp))) return rc;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_a = pb.add(rp.a.data(), T * sizeof(double));
+  const size_t o_s = pb.add(rp.s.data(), T * sizeof(double));
+  const size_t o_q = pb.add(rp.q.data(), T * sizeof(int));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_rotate(c, in, out, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q)))) return rc;
+  return end_call(c);
+}
+
+int graphic_adi_subtract(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *parang,
+                         double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if ((rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges))) return rc;
+  AdiPlanHost ap;
+  plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap);
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
+  const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
+  const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_adi(c, in, out, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2), n_edges - 1)))
+    return rc;
+  return end_call(c);
+}
+
+int graphic_collapse_median(graphic_ctx *c, const float *in, int64_t T, int32_t n, float *out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
+  DeviceGuard g(c->device);
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = enqueue_collapse(c, in, T, n, out))) return rc;
+  return end_call(c);
+}
+
+int graphic_reduce(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
+                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
+                   int32_t n_edges, float *out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, work, T, n);
+  if (rc) return rc;
+  if (!out) return fail(GRAPHIC_ERR_INVALID_ARG, "null out");
+  DeviceGuard g(c->device);
+  if ((rc = reduce_device(c, in, work, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, out))) {
+    cudaStreamSynchronize(c->stream);
+    c->ev_used = 0;
+    return rc;
+  }
+  return end_call(c);
+}
+
+int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t n, const double *dx,
+                        const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
+                        int32_t n_edges, float *host_out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(host_in, host_out, T, n);
+  if (rc) return rc;
+  if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
+  DeviceGuard g(c->device);
+  const size_t NN = (size_t)n * n;
+  if ((rc = ensure((void **)&c->d_cube, &c->cube_bytes, (size_t)T * NN * sizeof(float), false))) return rc;
+  if ((rc = ensure((void **)&c->d_img, &c->img_bytes, NN * sizeof(float), false))) return rc;
+  CK(cudaMemcpyAsync(c->d_cube, host_in, (size_t)T * NN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if ((rc = reduce_device(c, c->d_cube, c->d_cube, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, c->d_img))) {
+    cudaStreamSynchronize(c->stream);
+    c->ev_used = 0;
+    return rc;
+  }
+  CK(cudaMemcpyAsync(host_out, c->d_img, NN * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return end_call(c);
+}
+
+int graphic_profile(graphic_ctx *c, int enable) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  c->prof = enable != 0;
+  if (c->prof) {
+    for (int k = 0; k < GRAPHIC_K_COUNT; k++) {
+      c->prof_ms[k] = 0;
+      c->prof_n[k] = 0;
+    }
+  }
+  c->ev_used = 0;
+  return GRAPHIC_OK;
+}
+
+int graphic_profile_read(graphic_ctx *c, double *ms, int64_t *launches, int32_t n) {
+  if (!c || !ms || !launches || n < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  for (int32_t k = 0; k < n && k < GRAPHIC_K_COUNT; k++) {
+    ms[k] = c->prof_ms[k];
+    launches[k] = c->prof_n[k];
+  }
+  return GRAPHIC_OK;
+}
+
+const char *graphic_kernel_name(int32_t k) {
+  static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_median", "rot_pass1",
+                                              "rot_pass2", "rot_pass3", "collapse_median"};
+  return (k >= 0 && k < GRAPHIC_K_COUNT) ? names[k] : nullptr;
+}
+
+int graphic_workspace_bytes(graphic_ctx *c, int64_t *bytes) {
+  if (!c || !bytes) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->cube_bytes + c->img_bytes);
+  return GRAPHIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,563 @@
+// geom.cu -- Fourier line passes of the shift (Sect. 3.3.1) and of the
+// three-shear rotation (Sect. 3.4) on sm_103a.
+//
+// Every pass applies, to each line of a frame, the periodic Fourier shift
+//   v = IFFT_m( H(d) . FFT_m( u ) ),  H_k = exp(-i 2 pi k d / m) on signed
+//   bins k, H_{m/2} = cos(pi d) (a Hermitian filter, so real lines stay real)
+// where m = 2n is the zero-padded line length.  The padded line is handled
+// in "rolled" coordinates (padded index + n/2 mod m), so the frame data sit
+// in [0, n), the zero padding in [n, m) and the crop window of the output
+// is again [0, n): rolling commutes with a circular filter.
+//
+// Data path of one CTA (256 threads): it owns LPC = 4096/m line PAIRS, each
+// pair packed as one complex line z = a + i b (two real lines), handled by
+// m/16 threads holding 16 complex values in registers.  Forward FFT =
+// Stockham autosort stages of radix 16, 16 and m/256 (or 16, 8 for m = 128):
+// the first stage reads global memory straight into registers (input half
+// zero: pruned at compile time), later stages exchange through shared
+// memory (ping-pong buffers, one pad slot every 16 entries against bank
+// conflicts).  The middle step separates the two real spectra where the two
+// lines have different shifts (shear passes), multiplies by the phasors and
+// stores conj(V)/m; the inverse is then the same forward stages
+// (IFFT(V) = conj(FFT(conj V)) / m), the last stage writing the cropped
+// output straight to global memory.
+//
+// Phase arguments: d is formed in FP64 per line, reduced to delta = d/m =
+// delta_hi + delta_lo with delta_hi on a 2^-12 grid (so k * delta_hi is exact
+// in FP32 for k < 2^11) and the turns frac(k delta) evaluated as
+// (k delta_hi - rint(k delta_hi)) + k delta_lo before sincospif.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "graphic_internal.h"
+
+namespace graphic {
+namespace {
+
+// Twiddle tables W_m^e = exp(-i 2 pi e / m), e in [0, m), for m = 128..2048,
+// stored back to back at offset m - 128 (FP64 cos/sin rounded to FP32).
+constexpr int kTwTotal = 4096 - 128;
+__device__ float2 d_twiddle[kTwTotal];
+
+__host__ __device__ constexpr int tw_off(int m) { return m - 128; }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// exp(-i 2 pi j / 16) as (cos, sin) of 2 pi j / 16: the constants are
+// cos(pi/8), sin(pi/8) and sqrt(1/2).
+#define G_C16 0.92387953251128675613f
+#define G_S16 0.38268343236508977173f
+#define G_R2 0.70710678118654752440f
+
+template <int J>
+__device__ __forceinline__ float2 mul_w16(float2 a) {
+  constexpr int j = J & 15;
+  if constexpr (j == 0) return a;
+  else if constexpr (j == 4) return make_float2(a.y, -a.x);
+  else if constexpr (j == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (j == 12) return make_float2(-a.y, a.x);
+  else {
+    constexpr float cs[16] = {1.f, G_C16, G_R2, G_S16, 0.f, -G_S16, -G_R2, -G_C16,
+                              -1.f, -G_C16, -G_R2, -G_S16, 0.f, G_S16, G_R2, G_C16};
+    constexpr float sn[16] = {0.f, G_S16, G_R2, G_C16, 1.f, G_C16, G_R2, G_S16,
+                              0.f, -G_S16, -G_R2, -G_C16, -1.f, -G_C16, -G_R2, -G_S16};
+    constexpr float c = cs[j], s = sn[j];
+    // (a.x + i a.y)(c - i s)
+    return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+  }
+}
+
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = make_float2(t1.x + t3.y, t1.y - t3.x);  // t1 - i t3
+  a3 = make_float2(t1.x - t3.y, t1.y + t3.x);  // t1 + i t3
+}
+
+// In-place forward DFT of size R on a[0..R), natural order out.
+// R = R1 * R2 with n = R2 n1 + n2, k = k1 + R1 k2: inner DFT_R1 over n1,
+// twiddle W_R^(n2 k1), outer DFT_R2 over n2, then the index transpose.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&a)[R]);
+
+template <>
+__device__ __forceinline__ void dft<2>(float2 (&a)[2]) { dft2(a[0], a[1]); }
+
+template <>
+__device__ __forceinline__ void dft<4>(float2 (&a)[4]) { dft4(a[0], a[1], a[2], a[3]); }
+
+template <>
+__device__ __forceinline__ void dft<8>(float2 (&a)[8]) {
+  dft4(a[0], a[2], a[4], a[6]);
+  dft4(a[1], a[3], a[5], a[7]);
+  a[3] = mul_w16<2>(a[3]);   // n2 = 1, k1 = 1: W8^1
+  a[5] = mul_w16<4>(a[5]);   // k1 = 2
+  a[7] = mul_w16<6>(a[7]);   // k1 = 3
+  dft2(a[0], a[1]);
+  dft2(a[2], a[3]);
+  dft2(a[4], a[5]);
+  dft2(a[6], a[7]);
+  // slot 2 k1 + k2 holds X[k1 + 4 k2]
+  float2 t[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) t[i] = a[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+    for (int k2 = 0; k2 < 2; k2++) a[k1 + 4 * k2] = t[2 * k1 + k2];
+}
+
+template <>
+__device__ __forceinline__ void dft<16>(float2 (&a)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; n2++) dft4(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+  // slot 4 k1 + n2 *= W16^(n2 k1)
+  a[5] = mul_w16<1>(a[5]);
+  a[6] = mul_w16<2>(a[6]);
+  a[7] = mul_w16<3>(a[7]);
+  a[9] = mul_w16<2>(a[9]);
+  a[10] = mul_w16<4>(a[10]);
+  a[11] = mul_w16<6>(a[11]);
+  a[13] = mul_w16<3>(a[13]);
+  a[14] = mul_w16<6>(a[14]);
+  a[15] = mul_w16<9>(a[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++) dft4(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) t[i] = a[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; k2++) a[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// Radix of Stockham stage s (0-based) for line length M.
+template <int M, int S>
+struct Radix {
+  static constexpr int value = (S == 0) ? 16 : (S == 1 ? (M == 128 ? 8 : 16) : M / 256);
+};
+template <int M>
+struct NumStages {
+  static constexpr int value = (M <= 256) ? 2 : 3;
+};
+
+// One Stockham stage in registers: v[m] holds element j + m M/16 of the
+// stage input; after the call, v[u + U r] holds output r of virtual thread
+// vt = j + u M/16, to be stored at position (vt / NS) NS R + (vt % NS) + r NS.
+template <int M, int R, int NS>
+__device__ __forceinline__ void stage_compute(float2 (&v)[16], int j, const float2 *__restrict__ tw) {
+  constexpr int U = 16 / R;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int vt = j + u * (M / 16);
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) a[r] = v[u + U * r];
+    if constexpr (NS > 1) {
+      const int k = vt & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; r++) a[r] = cmul(a[r], __ldg(&tw[r * k * (M / (NS * R))]));
+    }
+    dft<R>(a);
+#pragma unroll
+    for (int r = 0; r < R; r++) v[u + U * r] = a[r];
+  }
+}
+
+template <int M, int R, int NS>
+__device__ __forceinline__ void stage_store_smem(const float2 (&v)[16], int j, float2 *dst) {
+  constexpr int U = 16 / R;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int vt = j + u * (M / 16);
+    const int base = (vt / NS) * NS * R + (vt & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; r++) dst[padi(base + r * NS)] = v[u + U * r];
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void load_smem(float2 (&v)[16], int j, const float2 *src) {
+#pragma unroll
+  for (int m = 0; m < 16; m++) v[m] = src[padi(j + m * (M / 16))];
+}
+
+// Stages 1.. of a forward transform from smem buffer `a` (ping-pong with
+// `b`); stage 0 has already been computed and stored into `a`.  Returns the
+// buffer holding the natural-order result (all stages but the last), or,
+// when LAST_TO_REGS, leaves the last stage's outputs in v.
+template <int M, bool LAST_TO_REGS>
+__device__ __forceinline__ float2 *run_stages(float2 (&v)[16], int j, float2 *a, float2 *b,
+                                              const float2 *__restrict__ tw) {
+  constexpr int S = NumStages<M>::value;
+  // stage 1
+  __syncthreads();
+  load_smem<M>(v, j, a);
+  stage_compute<M, Radix<M, 1>::value, 16>(v, j, tw);
+  if constexpr (S == 2) {
+    if constexpr (!LAST_TO_REGS) {
+      stage_store_smem<M, Radix<M, 1>::value, 16>(v, j, b);
+      return b;
+    }
+    return nullptr;
+  } else {
+    stage_store_smem<M, Radix<M, 1>::value, 16>(v, j, b);
+    __syncthreads();
+    load_smem<M>(v, j, b);
+    stage_compute<M, Radix<M, 2>::value, 256>(v, j, tw);
+    if constexpr (!LAST_TO_REGS) {
+      stage_store_smem<M, Radix<M, 2>::value, 256>(v, j, a);
+      return a;
+    }
+    return nullptr;
+  }
+}
+
+// Output position of register slot (u, r) after the last stage: vt + r M/R.
+template <int M>
+struct LastStage {
+  static constexpr int R = Radix<M, NumStages<M>::value - 1>::value;
+  static constexpr int U = 16 / R;
+};
+
+struct LineParam {
+  float dhi, dlo;   // delta = d / m split: delta_hi on a 2^-12 grid, delta_lo the rest
+  float cnyq;       // cos(pi d), Nyquist weight
+  float pad_;
+  float2 step[8];   // exp(-i 2 pi r delta), r = 0..7
+};
+
+__device__ __forceinline__ void make_param(LineParam &p, double d, int m) {
+  const double delta = d / (double)m;
+  const double dhi = rint(delta * 4096.0) / 4096.0;
+  p.dhi = (float)dhi;
+  p.dlo = (float)(delta - dhi);
+  const double d2 = d - 2.0 * rint(0.5 * d);   // d mod 2, exact
+  p.cnyq = cospif((float)d2);
+  p.pad_ = 0.f;
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    double t = (double)r * delta;
+    t -= rint(t);
+    float s, c;
+    sincospif(2.0f * (float)t, &s, &c);
+    p.step[r] = make_float2(c, -s);
+  }
+}
+
+// exp(-i 2 pi K delta) for integer 0 <= K < 2^11.
+__device__ __forceinline__ float2 phase_at(const LineParam &p, int K) {
+  float kf = (float)K;
+  float t = kf * p.dhi;      // exact: K < 2^11, dhi on a 2^-12 grid with |dhi| <= 1
+  t -= rintf(t);
+  t = fmaf(kf, p.dlo, t);
+  float s, c;
+  sincospif(2.0f * t, &s, &c);
+  return make_float2(c, -s);
+}
+
+template <int KIND>
+__device__ __forceinline__ double line_shift(const LineArgs &a, long long f, int line, int n) {
+  const int m = 2 * n;
+  if constexpr (KIND == SHIFT_X) return a.p0[f];
+  else if constexpr (KIND == SHIFT_Y) return a.p1[f];
+  else if constexpr (KIND == ROT_P2) return a.p1[f] * (double)(((line + n / 2) & (m - 1)) - n);
+  else return -a.p0[f] * (double)(line - n / 2);
+}
+
+__device__ __forceinline__ bool finite_pair(float2 v) { return isfinite(v.x) && isfinite(v.y); }
+
+// Load element `pos` (< n) of row `line` of rot90^q(frame) and of row line+1.
+__device__ __forceinline__ float2 load_rot90_pair(const float *__restrict__ fr, int n, int q, int line, int pos) {
+  float x0 = 0.f, x1 = 0.f;
+  switch (q) {
+    case 0:
+      x0 = fr[(size_t)line * n + pos];
+      x1 = fr[(size_t)(line + 1) * n + pos];
+      break;
+    case 1:   // g[i][j] = in[n - j][i]  (j >= 1)
+      if (pos >= 1) {
+        float2 t = *reinterpret_cast<const float2 *>(fr + (size_t)(n - pos) * n + line);
+        x0 = t.x;
+        x1 = t.y;
+      }
+      break;
+    case 2:   // g[i][j] = in[n - i][n - j]  (i, j >= 1)
+      if (pos >= 1) {
+        if (line >= 1) x0 = fr[(size_t)(n - line) * n + (n - pos)];
+        x1 = fr[(size_t)(n - line - 1) * n + (n - pos)];
+      }
+      break;
+    default:  // g[i][j] = in[j][n - i]  (i >= 1)
+      if (line >= 1) x0 = fr[(size_t)pos * n + (n - line)];
+      x1 = fr[(size_t)pos * n + (n - line - 1)];
+      break;
+  }
+  return make_float2(x0, x1);
+}
+
+template <int M, int KIND>
+__global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
+  constexpr int N = M / 2;
+  constexpr int TPL = M / 16;          // threads per line pair
+  constexpr int LPC = 4096 / M;        // line pairs per CTA
+  constexpr int LBUF = M + M / 16;     // padded line buffer, complex entries
+  constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
+  constexpr int NIN = (KIND == ROT_P3) ? M : N;        // input samples per line
+  constexpr int NOUT = (KIND == ROT_P1) ? M : N;       // output samples per line
+  constexpr int NLINES = (KIND == ROT_P2) ? M : N;     // lines per frame
+
+  extern __shared__ float2 smem[];
+  __shared__ LineParam lp[2 * LPC];
+  __shared__ int ident_s;
+
+  const int tid = threadIdx.x;
+  const int p = tid / TPL;
+  const int j = tid % TPL;
+  const long long f = blockIdx.y;
+  const int line0 = 2 * (blockIdx.x * LPC + p);
+  const float *__restrict__ fin = a.in + f * a.in_fstride;
+  float *__restrict__ fout = a.out + f * a.out_fstride;
+  const float2 *__restrict__ tw = d_twiddle + tw_off(M);
+  float2 *bufA = smem + p * LBUF;
+  float2 *bufB = smem + (LPC + p) * LBUF;
+  const int q = (KIND == ROT_P1) ? (a.q[f] & 3) : 0;
+
+  if (tid == 0) {
+    bool id;
+    if constexpr (KIND == SHIFT_X) id = (a.p0[f] == 0.0);
+    else if constexpr (KIND == SHIFT_Y) id = (a.p1[f] == 0.0);
+    else id = (a.p0[f] == 0.0 && a.p1[f] == 0.0);
+    ident_s = id ? 1 : 0;
+  }
+  if (tid < 2 * LPC && (!SAME_D || tid == 0)) {
+    const int gl = 2 * blockIdx.x * LPC + tid;
+    make_param(lp[tid], line_shift<KIND>(a, f, gl, N), M);
+  }
+  __syncthreads();
+
+  bool bad = false;
+  if (ident_s) {
+    // zero shift for every line of the frame: copy (exact identity)
+    if constexpr (KIND == ROT_P2) return;
+    for (int pos = j; pos < NOUT; pos += TPL) {
+      float2 z = make_float2(0.f, 0.f);
+      if (pos < NIN) {
+        if constexpr (KIND == SHIFT_X || KIND == ROT_P3) {
+          const int rs = (KIND == ROT_P3) ? M : N;
+          z = make_float2(fin[(size_t)line0 * rs + pos], fin[(size_t)(line0 + 1) * rs + pos]);
+        } else if constexpr (KIND == SHIFT_Y) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+        } else if constexpr (KIND == ROT_P1) {
+          z = load_rot90_pair(fin, N, q, line0, pos);
+        }
+      }
+      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+      if constexpr (KIND == SHIFT_Y) {
+        *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = z;
+      } else {
+        const int rs = (KIND == ROT_P1) ? M : N;
+        fout[(size_t)line0 * rs + pos] = z.x;
+        fout[(size_t)(line0 + 1) * rs + pos] = z.y;
+      }
+    }
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    return;
+  }
+
+  // ---- forward transform, stage 0 straight from global memory ----------
+  float2 v[16];
+#pragma unroll
+  for (int m = 0; m < 16; m++) {
+    const int pos = j + m * (M / 16);
+    float2 z = make_float2(0.f, 0.f);
+    if (m * (M / 16) < NIN) {   // compile-time pruning of the zero half
+      if constexpr (KIND == SHIFT_X) {
+        z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
+      } else if constexpr (KIND == SHIFT_Y) {
+        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+      } else if constexpr (KIND == ROT_P1) {
+        z = load_rot90_pair(fin, N, q, line0, pos);
+      } else if constexpr (KIND == ROT_P2) {
+        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
+      } else {
+        z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+      }
+      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+    }
+    v[m] = z;
+  }
+  if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+  }
+  stage_compute<M, 16, 1>(v, j, tw);
+  stage_store_smem<M, 16, 1>(v, j, bufA);
+  float2 *spec = run_stages<M, false>(v, j, bufA, bufB, tw);
+  __syncthreads();
+
+  // ---- middle: phasors (and separation of the two real spectra) ---------
+  {
+    const LineParam &la = lp[SAME_D ? 0 : 2 * p];
+    const LineParam &lb = lp[SAME_D ? 0 : 2 * p + 1];
+    const float inv_m = 1.0f / (float)M;
+    const int K0 = 8 * j;
+    const float2 ba = phase_at(la, K0);
+    const float2 bb = SAME_D ? ba : phase_at(lb, K0);
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      const int k = K0 + r;
+      if (k == 0) {
+        float2 z = spec[0];
+        spec[0] = make_float2(z.x * inv_m, -z.y * inv_m);
+        continue;
+      }
+      const float2 ha = cmul(ba, la.step[r]);
+      float2 z = spec[padi(k)], zm = spec[padi(M - k)];
+      float2 vk, vm;
+      if constexpr (SAME_D) {
+        vk = cmul(z, ha);
+        vm = cmul(zm, cconj(ha));
+      } else {
+        const float2 hb = cmul(bb, lb.step[r]);
+        // A = (Z_k + conj Z_{-k}) / 2,  B = (Z_k - conj Z_{-k}) / (2i)
+        const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+        const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+        const float2 P = cmul(A, ha), Q = cmul(B, hb);
+        vk = make_float2(P.x - Q.y, P.y + Q.x);     // P + i Q
+        vm = make_float2(P.x + Q.y, Q.x - P.y);     // conj P + i conj Q
+      }
+      spec[padi(k)] = make_float2(vk.x * inv_m, -vk.y * inv_m);
+      spec[padi(M - k)] = make_float2(vm.x * inv_m, -vm.y * inv_m);
+    }
+    if (j == 0) {
+      float2 z = spec[padi(M / 2)];
+      spec[padi(M / 2)] = make_float2(z.x * la.cnyq * inv_m, -z.y * lb.cnyq * inv_m);
+    }
+  }
+  __syncthreads();
+
+  // ---- inverse via forward stages on conj(V)/m --------------------------
+  float2 *other = (spec == bufA) ? bufB : bufA;
+  load_smem<M>(v, j, spec);
+  stage_compute<M, 16, 1>(v, j, tw);
+  stage_store_smem<M, 16, 1>(v, j, other);
+  run_stages<M, true>(v, j, other, spec, tw);
+
+  // ---- store: slot (u, r) -> position vt + r M/R; y = conj(result) -------
+  constexpr int RL = LastStage<M>::R;
+  constexpr int UL = LastStage<M>::U;
+#pragma unroll
+  for (int u = 0; u < UL; u++) {
+#pragma unroll
+    for (int r = 0; r < RL; r++) {
+      const int pos = j + u * (M / 16) + r * (M / RL);
+      if (r * (M / RL) < NOUT) {
+        const float2 y = v[u + UL * r];
+        if constexpr (KIND == SHIFT_Y) {
+          *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = make_float2(y.x, -y.y);
+        } else if constexpr (KIND == ROT_P2) {
+          *reinterpret_cast<float2 *>(fout + (size_t)pos * M + line0) = make_float2(y.x, -y.y);
+        } else {
+          const int rs = (KIND == ROT_P1) ? M : N;
+          fout[(size_t)line0 * rs + pos] = y.x;
+          fout[(size_t)(line0 + 1) * rs + pos] = -y.y;
+        }
+      }
+    }
+  }
+  (void)NLINES;
+}
+
+template <int M>
+size_t line_smem_bytes() {
+  constexpr int LPC = 4096 / M;
+  constexpr int LBUF = M + M / 16;
+  return (size_t)2 * LPC * LBUF * sizeof(float2);
+}
+
+template <int M, int KIND>
+cudaError_t launch_one(const LineArgs &a, long long n_frames, cudaStream_t st) {
+  constexpr int N = M / 2;
+  constexpr int LPC = 4096 / M;
+  constexpr int NLINES = (KIND == ROT_P2) ? M : N;
+  const size_t smem = line_smem_bytes<M>();
+  static bool configured = false;   // per process; attribute is per function
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(line_pass_kernel<M, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  for (long long f0 = 0; f0 < n_frames; f0 += 65535) {
+    const long long nf = (n_frames - f0 < 65535) ? (n_frames - f0) : 65535;
+    LineArgs b = a;
+    b.in = a.in + f0 * a.in_fstride;
+    b.out = a.out + f0 * a.out_fstride;
+    b.p0 = a.p0 ? a.p0 + f0 : nullptr;
+    b.p1 = a.p1 ? a.p1 + f0 : nullptr;
+    b.q = a.q ? a.q + f0 : nullptr;
+    dim3 grid(NLINES / (2 * LPC), (unsigned)nf);
+    line_pass_kernel<M, KIND><<<grid, 256, smem, st>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int M>
+cudaError_t launch_m(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st) {
+  switch (kind) {
+    case SHIFT_X: return launch_one<M, SHIFT_X>(a, n_frames, st);
+    case SHIFT_Y: return launch_one<M, SHIFT_Y>(a, n_frames, st);
+    case ROT_P1: return launch_one<M, ROT_P1>(a, n_frames, st);
+    case ROT_P2: return launch_one<M, ROT_P2>(a, n_frames, st);
+    case ROT_P3: return launch_one<M, ROT_P3>(a, n_frames, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int geom_init_device() {
+  static float2 host[kTwTotal];
+  static bool filled = false;
+  if (!filled) {
+    for (int m = 128; m <= 2048; m *= 2)
+      for (int e = 0; e < m; e++) {
+        const double ang = 2.0 * 3.14159265358979323846 * (double)e / (double)m;
+        host[tw_off(m) + e] = make_float2((float)cos(ang), (float)-sin(ang));
+      }
+    filled = true;
+  }
+  return cudaMemcpyToSymbol(d_twiddle, host, sizeof(host)) == cudaSuccess ? 0 : -1;
+}
+
+cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st) {
+  if (n_frames <= 0) return cudaSuccess;
+  switch (a.n) {
+    case 64: return launch_m<128>(kind, a, n_frames, st);
+    case 128: return launch_m<256>(kind, a, n_frames, st);
+    case 256: return launch_m<512>(kind, a, n_frames, st);
+    case 512: return launch_m<1024>(kind, a, n_frames, st);
+    case 1024: return launch_m<2048>(kind, a, n_frames, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace graphic

@@ -1,0 +1,61 @@
+// Internal declarations shared by the CUDA translation units of the GRAPHIC
+// GB300 library.  Not part of the C ABI (see include/graphic.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace graphic {
+
+// Line-pass kinds: which lines of which buffer one launch transforms.
+//   SHIFT_X  rows of an n x n frame, shift dx[f]             (Sect. 3.3.1)
+//   SHIFT_Y  columns of an n x n frame, shift dy[f]          (Sect. 3.3.1)
+//   ROT_P1   rows of rot90^q(frame) -> scratch rows of 2n, x-shear -a y (Sect. 3.4)
+//   ROT_P2   columns of the n x 2n scratch, y-shear +s x     (Sect. 3.4)
+//   ROT_P3   scratch rows -> frame rows, x-shear -a y        (Sect. 3.4)
+enum LineKind { SHIFT_X = 0, SHIFT_Y = 1, ROT_P1 = 2, ROT_P2 = 3, ROT_P3 = 4 };
+
+struct LineArgs {
+  const float *in;       // frame cube (SHIFT_*, ROT_P1) or scratch (ROT_P2/P3)
+  float *out;            // frame cube (SHIFT_*, ROT_P3) or scratch (ROT_P1/P2)
+  const double *p0;      // per frame: dx (SHIFT_X) or a = tan(theta'/2) (ROT_*)
+  const double *p1;      // per frame: dy (SHIFT_Y) or s = sin(theta') (ROT_*)
+  const int *q;          // per frame: quarter turns (ROT_P1)
+  int *status;           // device status word (bit 0: non-finite input)
+  long long in_fstride;  // elements between consecutive frames of `in`
+  long long out_fstride; // elements between consecutive frames of `out`
+  int n;                 // frame side
+};
+
+// Device status bits.
+constexpr int STATUS_NONFINITE = 1;
+constexpr int STATUS_INTERNAL = 2;
+
+// geom.cu
+int geom_init_device();   // uploads the twiddle tables of the current device (0 = ok)
+cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st);
+
+// median.cu
+struct AdiArgs {
+  const float *in;
+  float *out;
+  const int *perm;       // [T] frame index at angle-sorted position s
+  const int *lr;         // [A][T][2] (L, R) of the reference set of sorted frame s in annulus a
+  const double *edge2;   // [A+1] squared annulus edges (FP64)
+  int *status;
+  int T;
+  int n;
+  int n_ann;             // A
+};
+cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st);
+
+struct CollapseArgs {
+  const float *in;
+  float *out;
+  int *status;
+  long long T;
+  int n;
+};
+cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st);
+
+}  // namespace graphic

@@ -1,0 +1,267 @@
+"""Python binding of the C ABI in ``include/graphic.h`` (ctypes).
+
+Argument marshalling only: every step runs in the CUDA library
+``libgraphic.so``.  There is no CPU fallback; if the library is missing or
+fails to load, every call raises :class:`GraphicError`.
+
+Cubes are torch CUDA float32 tensors of shape (T, n, n) (C-contiguous);
+per-frame parameters are anything numpy turns into float64 arrays.  Calls run
+on the current torch CUDA stream of the cube's device and return when the
+device work is done.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgraphic.so")
+
+GRAPHIC_OK = 0
+ERRORS = {
+    -1: "GRAPHIC_ERR_INVALID_ARG",
+    -2: "GRAPHIC_ERR_UNSUPPORTED",
+    -3: "GRAPHIC_ERR_OOM",
+    -4: "GRAPHIC_ERR_CUDA",
+    -5: "GRAPHIC_ERR_NONFINITE",
+    -6: "GRAPHIC_ERR_TIMEOUT",
+    -7: "GRAPHIC_ERR_INTERNAL",
+}
+KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median"]
+MAX_FRAMES_MEDIAN = 2048
+
+
+class GraphicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+# name -> argtypes, following include/graphic.h
+_SIGS = {
+    "graphic_create": [ctypes.POINTER(_P), ctypes.c_int],
+    "graphic_destroy": [_P],
+    "graphic_release": [_P],
+    "graphic_set_stream": [_P, _P],
+    "graphic_last_error": [],
+    "graphic_version": [],
+    "graphic_shift": [_P, _P, _P, _I64, _I32, _D, _D],
+    "graphic_rotate": [_P, _P, _P, _I64, _I32, _D],
+    "graphic_adi_subtract": [_P, _P, _P, _I64, _I32, _D, ctypes.c_double, ctypes.c_double, _D, _I32],
+    "graphic_collapse_median": [_P, _P, _I64, _I32, _P],
+    "graphic_reduce": [_P, _P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
+    "graphic_reduce_host": [_P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
+    "graphic_profile": [_P, ctypes.c_int],
+    "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
+    "graphic_kernel_name": [_I32],
+    "graphic_workspace_bytes": [_P, ctypes.POINTER(_I64)],
+}
+
+
+def lib():
+    """Load ``libgraphic.so`` (raises GraphicError when it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise GraphicError(-4, f"CUDA library not built ({LIB_PATH}); run paper_1510_04331_gb300.build.build()")
+            try:
+                L = ctypes.CDLL(LIB_PATH)
+            except OSError as e:  # pragma: no cover
+                raise GraphicError(-4, f"cannot load {LIB_PATH}: {e}")
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.graphic_last_error.restype = ctypes.c_char_p
+            L.graphic_kernel_name.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != GRAPHIC_OK:
+        raise GraphicError(rc, lib().graphic_last_error().decode())
+
+
+def _f64(x, T):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), (T,)))
+    return a, a.ctypes.data_as(_D)
+
+
+def _cube(t, name="cube"):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 3
+            and t.is_contiguous() and t.shape[1] == t.shape[2]):
+        raise GraphicError(-1, f"{name} must be a contiguous CUDA float32 tensor of shape (T, n, n)")
+    return t
+
+
+class Context:
+    """A library context bound to one CUDA device (owns its workspaces)."""
+
+    def __init__(self, device: int = 0):
+        h = _P()
+        _check(lib().graphic_create(ctypes.byref(h), int(device)))
+        self.h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().graphic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _check(lib().graphic_set_stream(self.h, _P(s)))
+
+    def graphic_shift(self, cube, dx, dy, out=None):
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty_like(cube) if out is None else _cube(out, "out")
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        self._stream()
+        _check(lib().graphic_shift(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, pdx, pdy))
+        return out
+
+    def graphic_rotate(self, cube, theta_deg, out=None):
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty_like(cube) if out is None else _cube(out, "out")
+        tha, pth = _f64(theta_deg, T)
+        self._stream()
+        _check(lib().graphic_rotate(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, pth))
+        return out
+
+    def graphic_adi_subtract(self, cube, parang, fwhm, n_fwhm, edges, out=None):
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty_like(cube) if out is None else _cube(out, "out")
+        paa, ppa = _f64(parang, T)
+        ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
+        self._stream()
+        _check(lib().graphic_adi_subtract(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, ppa,
+                                          float(fwhm), float(n_fwhm), ea.ctypes.data_as(_D), ea.size))
+        return out
+
+    def graphic_collapse_median(self, cube, out=None):
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty((n, n), dtype=torch.float32, device=cube.device) if out is None else out
+        self._stream()
+        _check(lib().graphic_collapse_median(self.h, _P(cube.data_ptr()), T, n, _P(out.data_ptr())))
+        return out
+
+    def graphic_reduce(self, cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None):
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        work = torch.empty_like(cube) if work is None else _cube(work, "work")
+        out = torch.empty((n, n), dtype=torch.float32, device=cube.device) if out is None else out
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        paa, ppa = _f64(parang, T)
+        ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
+        self._stream()
+        _check(lib().graphic_reduce(self.h, _P(cube.data_ptr()), _P(work.data_ptr()), T, n, pdx, pdy, ppa,
+                                    float(fwhm), float(n_fwhm), ea.ctypes.data_as(_D), ea.size,
+                                    _P(out.data_ptr())))
+        return out
+
+    def graphic_reduce_host(self, cube_host, dx, dy, parang, fwhm, n_fwhm, edges, out_host=None):
+        """Host buffers in, host result out (the library copies both ways).
+        ``cube_host`` is a float32 numpy array or a (pinned) CPU torch tensor."""
+        if hasattr(cube_host, "data_ptr"):
+            T, n = int(cube_host.shape[0]), int(cube_host.shape[1])
+            ptr = cube_host.data_ptr()
+        else:
+            cube_host = np.ascontiguousarray(cube_host, dtype=np.float32)
+            T, n = cube_host.shape[0], cube_host.shape[1]
+            ptr = cube_host.ctypes.data
+        if out_host is None:
+            out_host = np.empty((n, n), np.float32)
+        optr = out_host.data_ptr() if hasattr(out_host, "data_ptr") else out_host.ctypes.data
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        paa, ppa = _f64(parang, T)
+        ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
+        self._stream()
+        _check(lib().graphic_reduce_host(self.h, _P(ptr), T, n, pdx, pdy, ppa, float(fwhm), float(n_fwhm),
+                                         ea.ctypes.data_as(_D), ea.size, _P(optr)))
+        return out_host
+
+    def profile(self, enable: bool):
+        _check(lib().graphic_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        n = len(KERNELS)
+        ms = (ctypes.c_double * n)()
+        cnt = (_I64 * n)()
+        _check(lib().graphic_profile_read(self.h, ms, cnt, n))
+        return {KERNELS[k]: (ms[k], cnt[k]) for k in range(n)}
+
+    def workspace_bytes(self) -> int:
+        b = _I64()
+        _check(lib().graphic_workspace_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def release(self):
+        _check(lib().graphic_release(self.h))
+
+
+_ctx = {}
+
+
+def context(device=None) -> Context:
+    """Default per-device context."""
+    import torch
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _ctx:
+        _ctx[d] = Context(d)
+    return _ctx[d]
+
+
+def graphic_shift(cube, dx, dy, out=None):
+    return context(cube.device.index).graphic_shift(cube, dx, dy, out)
+
+
+def graphic_rotate(cube, theta_deg, out=None):
+    return context(cube.device.index).graphic_rotate(cube, theta_deg, out)
+
+
+def graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out=None):
+    return context(cube.device.index).graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out)
+
+
+def graphic_collapse_median(cube, out=None):
+    return context(cube.device.index).graphic_collapse_median(cube, out)
+
+
+def graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None):
+    return context(cube.device.index).graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work, out)
+
+
+def graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, device=0, out_host=None):
+    return context(device).graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, out_host)
