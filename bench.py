@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the GRAPHIC ADI hot path on GB300.
+
+One step = one full reduction (recentring shift, angle-gated median PSF
+subtraction, three-shear derotation, median collapse) of one synthetic cube
+of 2000 frames of 512 x 512 (padded to 1024), through the C ABI
+(graphic_reduce).  Prints ONE JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 is launched with torch.distributed.run: every rank reduces its own cube
+(independent problems, no collective on the data path), the elapsed time is
+the max over ranks and the value counts the frames of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s (1024² FFT shift+3-shear derot) & % HBM roofline; p50/p99 latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "survey": dict(T=2000, n=512, seed=1,
+                   desc="2000 frames of 512x512 (padded to 1024), alt-az parallactic angles (dec -30, lat -24.6, "
+                        "h -1.5..+1.5 h), AR(1) speckles rho=0.99, 5 companions 10-100 px, contrast 1e-3..1e-5; "
+                        "full reduce: shift, median PSF subtraction, 3-shear derotation, median collapse"),
+    "small": dict(T=32, n=128, seed=0,
+                  desc="32 frames of 128x128 (padded to 256), angles 0-40 deg, 2 companions; full reduce"),
+}
+
+
+def make_workload(name):
+    from paper_1510_04331_gb300 import synth
+    w = WORKLOADS[name]
+    if name == "survey":
+        return synth.survey_cube(seed=w["seed"], T=w["T"], N=w["n"])
+    return synth.small_cube(seed=w["seed"], T=w["T"], N=w["n"])
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per kernel launch (bytes or flops), per frame of side n
+# ---------------------------------------------------------------------------
+
+def fft_flops_per_frame(kind, n):
+    """Nominal 5 m log2 m flops per complex m-point FFT, forward + inverse,
+    two real lines per complex transform (m = 2n)."""
+    m = 2 * n
+    lines = {"shift_x": n, "shift_y": n, "rot_pass1": n, "rot_pass2": m, "rot_pass3": n}[kind]
+    return (lines / 2) * 2 * 5 * m * math.log2(m)
+
+
+def kernel_work(kind, n, T):
+    """(bound, algorithmic amount per launch-frame, unit) for one frame."""
+    if kind in ("shift_x", "shift_y", "rot_pass1", "rot_pass2", "rot_pass3"):
+        return "alu", fft_flops_per_frame(kind, n), "flop"
+    if kind == "adi_median":
+        return "hbm", 2 * n * n * 4, "B"
+    return "hbm", n * n * 4, "B"   # collapse: read the cube once
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid_or_index(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return dev
+
+
+# ---------------------------------------------------------------------------
+# oracle CPU baseline (a bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(d, budget_s=15.0):
+    import oracle
+    T, n = d.cube.shape[0], d.cube.shape[1]
+    nt = oracle.num_threads()
+    k = max(1, min(T, nt))
+    fr = np.linspace(0, T - 1, k).astype(int)
+    c64 = d.cube[fr].astype(np.float64)
+    t0 = time.perf_counter()
+    sh = oracle.shift(c64, d.dx[fr], d.dy[fr])
+    t1 = time.perf_counter()
+    oracle.rotate(sh, -d.parang[fr])
+    t2 = time.perf_counter()
+    per_frame_geom = (t2 - t0) / k
+    # median stages on a few pixels of the whole cube
+    rng = np.random.default_rng(0)
+    npix = max(1, nt)
+    pix = rng.choice(n * n, npix, replace=False)
+    t3 = time.perf_counter()
+    oracle.adi_subtract(d.cube.astype(np.float32), d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix)
+    t4 = time.perf_counter()
+    per_pix_adi = (t4 - t3) / npix
+    # scale the pixel sample up if the first round was short
+    extra = max(0.0, budget_s - (t4 - t0))
+    if extra > 1.0 and per_pix_adi > 0:
+        more = int(min(extra / per_pix_adi * 0.8, 64 * npix))
+        if more >= 1:
+            pix2 = rng.choice(n * n, more, replace=False)
+            t5 = time.perf_counter()
+            oracle.adi_subtract(d.cube.astype(np.float32), d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix2)
+            t6 = time.perf_counter()
+            per_pix_adi = ((t4 - t3) + (t6 - t5)) / (npix + more)
+            npix += more
+    t7 = time.perf_counter()
+    cp = rng.choice(n * n, min(n * n, 4096), replace=False)
+    oracle.collapse_median(d.cube.astype(np.float64), pixels=cp)
+    t8 = time.perf_counter()
+    per_pix_col = (t8 - t7) / cp.size
+    sec_per_cube = per_frame_geom * T + (per_pix_adi + per_pix_col) * n * n
+    return {
+        "value": T / sec_per_cube, "unit": "frames/s", "cores": nt, "kind": "oracle",
+        "sample": (f"FP64 oracle on {k} frames (shift + 3-shear rotation, {per_frame_geom:.3f} s/frame), "
+                   f"median PSF subtraction on {npix} pixels x {T} frames ({per_pix_adi:.4f} s/pixel) and "
+                   f"median collapse on {cp.size} pixels, scaled to the {T}x{n}x{n} cube"),
+        "sec_per_cube": sec_per_cube,
+    }
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    name = args.workload
+    d = make_workload(name)
+    T, n = d.cube.shape[0], d.cube.shape[1]
+    vals = []
+    # each step is one bounded oracle sample; the whole run stays within a few minutes
+    budget = min(args.ref_budget, max(2.0, 150.0 / (args.warmup + args.steps)))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(d, budget_s=budget)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    sec = T / v
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[name]["desc"], "frames": T, "n": n, "m": 2 * n},
+        "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"] + "; each step times one such sample"},
+        "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1510_04331_gb300 import graphic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name = args.workload
+    d = make_workload(name)
+    T, n = d.cube.shape[0], d.cube.shape[1]
+    NN = n * n
+    ctx = graphic.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    cube = torch.from_numpy(d.cube).to(dev)
+    work = torch.empty_like(cube)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.graphic_reduce(cube, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges, work=work, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(gpu_uuid_or_index(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    ctx.profile(True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames_total = T * args.steps * world
+    value = frames_total / (total_ms / 1e3)
+
+    # e2e: host buffers through graphic_reduce_host, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(d.cube).pin_memory()
+        hout = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        ne = max(2, min(args.steps, args.e2e_steps))
+        for _ in range(2):
+            ctx.graphic_reduce_host(host, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges, out_host=hout)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            ctx.graphic_reduce_host(host, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges, out_host=hout)
+        el = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": T * ne * world / el, "unit": "frames/s", "h2d_bytes_per_step": T * NN * 4,
+               "d2h_bytes_per_step": NN * 4, "steps": ne}
+
+    if rank != 0:
+        return 0
+    # per-kernel table and the dominant kernel's roofline
+    hbm_peak, peak_src = peaks()
+    kernels = {}
+    for kname, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        kernels[kname] = {"ms_per_step": ms / args.steps, "launches_per_step": cnt / args.steps,
+                          "avg_launch_ms": ms / cnt}
+    ktot = sum(k["ms_per_step"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["ms_per_step"] / ktot if ktot else None
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    kd = kernels[dom]
+    frames_per_launch = T / kd["launches_per_step"]
+    bound, per_frame, unit = kernel_work(dom, n, T)
+    amount = per_frame * frames_per_launch
+    avg_s = kd["avg_launch_ms"] / 1e3
+    if bound == "hbm":
+        achieved = amount / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "kernel": dom, "peak_source": peak_src + " (copy, MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_per_launch": amount}
+    else:
+        achieved = amount / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
+                "algorithmic_per_launch": amount}
+    # whole-step HBM roofline (algorithmic 7 n^2 4 B per frame)
+    alg_bytes = 7 * NN * 4 * T
+    step_s = statistics.median(step_ms) / 1e3
+    whole = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / step_s / 1e9,
+             "frac_of_hbm": alg_bytes / step_s / 1e9 / hbm_peak}
+    srt = sorted(step_ms)
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[name]["desc"], "frames": T, "n": n, "m": 2 * n,
+                   "l2": "inputs larger than L2 (cube %.2f GB per rank)" % (T * NN * 4 / 1e9),
+                   "parallelism": f"{world} independent cubes (one per GPU)"},
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
+        "roofline": roof,
+        "whole_step_hbm": whole,
+        "kernels": kernels,
+        "gpu_launches": int(round(sum(k["launches_per_step"] for k in kernels.values()) * args.steps)),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(d, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    elif not args.no_cpu_baseline:
+        line["cpu_baseline"] = None
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())
