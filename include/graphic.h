@@ -141,6 +141,29 @@ int graphic_reduce_host(graphic_ctx *ctx, const float *host_in, int64_t n_frames
                         const double *dy, const double *parang_deg, double fwhm, double n_fwhm,
                         const double *annuli_edges, int32_t n_edges, float *host_out);
 
+/*
+ * graphic_rotate without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (an allocator policy that forbids it, a host application that
+ * hands over only a stream and pre-allocated buffers, a path that must not
+ * trigger allocator work).  Same arithmetic and result as graphic_rotate;
+ * in, out: device cubes of the caller, n_frames x n x n floats; theta_deg:
+ * host array of n_frames doubles; stream: cudaStream_t (NULL = legacy
+ * default stream); runs on the CURRENT CUDA device and waits for `stream`.
+ * No context is needed.  Its working memory is a 16 MiB static device
+ * array inside the library (plus a small static plan array), which every
+ * GPU that loads the library holds until the process exits; frames go
+ * through it in chunks of 16 MiB / (8 n^2) frames.  A frame whose n x 2n
+ * scratch exceeds 16 MiB is rejected with GRAPHIC_ERR_UNSUPPORTED.  The
+ * first call on a device sets the device up (takes the static arrays'
+ * device addresses, uploads the FFT tables): make that first call before
+ * any stream capture.  All calls share the static arrays: calls that
+ * overlap on the GPU (other streams, other host threads) race; serialise
+ * them.
+ */
+int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_t n, const double *theta_deg,
+                           void *stream);
+
 /* ---- measurement support ------------------------------------------------ */
 
 /* Kernel identifiers for graphic_profile_read. */

@@ -456,6 +456,8 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
 
 }  // namespace
 
+int graphic::set_last_error(int code, const char *msg) { return fail(code, msg); }
+
 extern "C" {
 
 int graphic_version(void) { return 10000; }

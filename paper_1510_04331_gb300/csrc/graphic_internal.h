@@ -27,6 +27,10 @@ struct LineArgs {
   int n;                 // frame side
 };
 
+// Record `msg` as the calling thread's last error (graphic_last_error) and
+// return `code` (capi.cu).
+int set_last_error(int code, const char *msg);
+
 // Device status bits.
 constexpr int STATUS_NONFINITE = 1;
 constexpr int STATUS_INTERNAL = 2;

@@ -64,6 +64,7 @@ _SIGS = {
     "graphic_profile": [_P, ctypes.c_int],
     "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
     "graphic_kernel_name": [_I32],
+    "graphic_rotate_noalloc": [_P, _P, _I64, _I32, _D, _P],
     "graphic_workspace_bytes": [_P, ctypes.POINTER(_I64)],
 }
 
@@ -261,6 +262,21 @@ def graphic_collapse_median(cube, out=None):
 
 def graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None):
     return context(cube.device.index).graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work, out)
+
+
+def graphic_rotate_noalloc(cube, theta_deg, out):
+    """Rotation through the entry point that allocates no device memory
+    (its working memory is a fixed static array in the library).  ``out``
+    must be given: this path creates nothing on the device itself."""
+    import torch
+    cube = _cube(cube)
+    out = _cube(out, "out")
+    T, n = cube.shape[0], cube.shape[1]
+    tha, pth = _f64(theta_deg, T)
+    s = torch.cuda.current_stream(cube.device).cuda_stream
+    with torch.cuda.device(cube.device):
+        _check(lib().graphic_rotate_noalloc(_P(cube.data_ptr()), _P(out.data_ptr()), T, n, pth, _P(s)))
+    return out
 
 
 def graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, device=0, out_host=None):
