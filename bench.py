@@ -46,12 +46,24 @@ WORKLOADS = {
 }
 
 
-def make_workload(name):
+def make_workload(name, frames=None, n=None):
     from paper_1510_04331_gb300 import synth
-    w = WORKLOADS[name]
+    w = dict(WORKLOADS[name])
+    if frames:
+        w["T"] = frames
+    if n:
+        w["n"] = n
     if name == "survey":
         return synth.survey_cube(seed=w["seed"], T=w["T"], N=w["n"])
     return synth.small_cube(seed=w["seed"], T=w["T"], N=w["n"])
+
+
+def workload_desc(name, d):
+    T, n = d.cube.shape[0], d.cube.shape[1]
+    w = WORKLOADS[name]
+    if (T, n) == (w["T"], w["n"]):
+        return w["desc"]
+    return f"{T} frames of {n}x{n} (padded to {2 * n}), {name} recipe; full reduce"
 
 
 def peaks():
@@ -203,7 +215,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     name = args.workload
-    d = make_workload(name)
+    d = make_workload(name, args.frames, args.n)
     T, n = d.cube.shape[0], d.cube.shape[1]
     vals = []
     # each step is one bounded oracle sample; the whole run stays within a few minutes
@@ -218,7 +230,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name]["desc"], "frames": T, "n": n, "m": 2 * n},
+        "config": {"workload": workload_desc(name, d), "frames": T, "n": n, "m": 2 * n},
         "cpu_baseline": {"value": v, "unit": "frames/s", "cores": cb["cores"], "kind": "oracle",
                          "sample": cb["sample"] + "; each step times one such sample"},
         "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -234,7 +246,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     name = args.workload
-    d = make_workload(name)
+    d = make_workload(name, args.frames, args.n)
     T, n = d.cube.shape[0], d.cube.shape[1]
     NN = n * n
     ctx = graphic.Context(local_rank)
@@ -345,7 +357,7 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[name]["desc"], "frames": T, "n": n, "m": 2 * n,
+        "config": {"workload": workload_desc(name, d), "frames": T, "n": n, "m": 2 * n,
                    "l2": "inputs larger than L2 (cube %.2f GB per rank)" % (T * NN * 4 / 1e9),
                    "parallelism": f"{world} independent cubes (one per GPU)"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
@@ -372,6 +384,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS))
+    ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

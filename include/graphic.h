@@ -9,6 +9,8 @@
  *     frames) in DEVICE memory owned by the caller, except in the *_host
  *     calls, whose cube and result pointers are HOST memory.  n is a power
  *     of two in [64, 1024]; the frame centre is pixel (row n/2, col n/2).
+ *     Device cubes and results start on a 16-byte boundary (cudaMalloc and
+ *     torch give 256); GRAPHIC_ERR_INVALID_ARG otherwise.
  *   - Per-frame parameter arrays (dx, dy, theta, parang) are HOST arrays of
  *     n_frames doubles, owned by the caller, read before the call returns.
  *   - n_frames == 0 is a no-op for graphic_shift and graphic_rotate (the

@@ -89,9 +89,11 @@ struct DeviceGuard {
 
 bool supported_n(int32_t n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
 
-int check_cube(const void *in, const void *out, int64_t T, int32_t n) {
+int check_cube(const void *in, const void *out, int64_t T, int32_t n, bool device = true) {
   if (T < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 0");
   if (T > 0 && (!in || !out)) return fail(GRAPHIC_ERR_INVALID_ARG, "null cube pointer");
+  if (device && (((uintptr_t)in | (uintptr_t)out) & 15))
+    return fail(GRAPHIC_ERR_INVALID_ARG, "device cubes must be 16-byte aligned");
   if (!supported_n(n)) return fail(GRAPHIC_ERR_UNSUPPORTED, "n must be one of 64, 128, 256, 512, 1024");
   return GRAPHIC_OK;
 }
@@ -325,7 +327,36 @@ struct AdiPlanHost {
   std::vector<int> perm;
   std::vector<int> lr;      // [A][T][2]
   std::vector<double> edge2;
+  std::vector<int> band;    // [A][4]
+  int wmax = 0;
 };
+
+// Band of full ranks that holds every median annulus `lr` needs: query s has
+// |S| = L + T - R members, its (lower) median is the k-th of S, k = (|S|-1)/2,
+// and at most w = R - L frames are excluded, so that element has full rank in
+// [k, k + w]; with the upper median of an even |S|, in [k, k + 1 + w].
+void plan_band(const int *lr, int64_t T, int *out) {
+  int64_t blo = T, bhi = -1;
+  for (int64_t s = 0; s < T; s++) {
+    const int64_t L = lr[2 * s], R = lr[2 * s + 1];
+    const int64_t nS = L + (T - R), w = R - L;
+    const int64_t k = (nS - 1) / 2;
+    blo = std::min(blo, k);
+    bhi = std::max(bhi, k + ((nS & 1) ? 0 : 1) + w);
+  }
+  bhi = std::min<int64_t>(bhi, T - 1);
+  const int64_t B = bhi - blo + 1;
+  int W = 0;
+  for (int c = 1; c <= 32; c <<= 1)
+    if (32 * c >= B) {
+      W = c;
+      break;
+    }
+  out[0] = (int)blo;
+  out[1] = (int)bhi;
+  out[2] = W;
+  out[3] = 0;
+}
 
 double alpha_min_deg(double fwhm, double n_fwhm, double r) {
   double arg = n_fwhm * fwhm / (2.0 * r);
@@ -382,16 +413,31 @@ void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const
       lr[2 * s + 1] = (int)R;
     }
   }
+  ap.band.assign((size_t)A * 4, 0);
+  ap.wmax = 0;
+  for (int a = 0; a < A; a++) {
+    const int *lr = ap.lr.data() + (size_t)a * T * 2;
+    plan_band(lr, T, ap.band.data() + 4 * a);
+    // the band kernel's sweep needs gates that only move forward
+    for (int64_t s = 1; s < T; s++)
+      if (lr[2 * s] < lr[2 * s - 2] || lr[2 * s + 1] < lr[2 * s - 1]) {
+        ap.band[4 * a + 2] = 0;
+        break;
+      }
+    ap.wmax = std::max(ap.wmax, ap.band[4 * a + 2]);
+  }
 }
 
 int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
-                const int *p_lr, const double *p_edge2, int n_ann) {
+                const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann) {
   AdiArgs a{};
   a.in = in;
   a.out = out;
   a.perm = p_perm;
   a.lr = p_lr;
   a.edge2 = p_edge2;
+  a.band = p_band;
+  a.wmax = wmax;
   a.status = c->d_status;
   a.T = (int)T;
   a.n = n;
@@ -443,11 +489,12 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   const size_t o_q = pb.add(rp.q.data(), T * sizeof(int));
   const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
   const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
+  const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
   if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
   if ((rc = enqueue_adi(c, work, work, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
-                        n_edges - 1)))
+                        at<int>(c, o_band), ap.wmax, n_edges - 1)))
     return rc;
   if ((rc = enqueue_rotate(c, work, work, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q)))) return rc;
   if ((rc = enqueue_collapse(c, work, T, n, out))) return rc;
@@ -577,9 +624,11 @@ int graphic_adi_subtract(graphic_ctx *c, const float *in, float *out, int64_t T,
   const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
   const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
   const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
+  const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
-  if ((rc = enqueue_adi(c, in, out, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2), n_edges - 1)))
+  if ((rc = enqueue_adi(c, in, out, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
+                        at<int>(c, o_band), ap.wmax, n_edges - 1)))
     return rc;
   return end_call(c);
 }
@@ -615,7 +664,7 @@ int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t
                         const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
                         int32_t n_edges, float *host_out) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
-  int rc = check_cube(host_in, host_out, T, n);
+  int rc = check_cube(host_in, host_out, T, n, false);
   if (rc) return rc;
   if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
   DeviceGuard g(c->device);

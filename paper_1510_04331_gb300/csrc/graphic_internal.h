@@ -46,10 +46,13 @@ struct AdiArgs {
   const int *perm;       // [T] frame index at angle-sorted position s
   const int *lr;         // [A][T][2] (L, R) of the reference set of sorted frame s in annulus a
   const double *edge2;   // [A+1] squared annulus edges (FP64)
+  const int *band;       // [A][4] (blo, bhi, W, 0): full-rank band holding every median the
+                         // annulus needs, W = bitmap words per lane (0: general path)
   int *status;
   int T;
   int n;
   int n_ann;             // A
+  int wmax;              // largest W over the annuli (0: no band path)
 };
 cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st);
 

@@ -43,6 +43,29 @@ __device__ __forceinline__ float key2f(uint32_t k) {
   return __uint_as_float(b);
 }
 
+// 16-byte asynchronous global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Position of the (r+1)-th set bit of x (r = 0 for the lowest), r < popc(x):
+// bisection on the popcounts of the low 16, 8, 4, 2 and 1 bits.
+__device__ __forceinline__ int nth_set(uint32_t x, int r) {
+  int pos = 0, c;
+  c = __popc(x & 0xffffu);
+  if (r >= c) { r -= c; x >>= 16; pos += 16; }
+  c = __popc(x & 0xffu);
+  if (r >= c) { r -= c; x >>= 8; pos += 8; }
+  c = __popc(x & 0xfu);
+  if (r >= c) { r -= c; x >>= 4; pos += 4; }
+  c = __popc(x & 0x3u);
+  if (r >= c) { r -= c; x >>= 2; pos += 2; }
+  if (r >= (int)(x & 1u)) pos += 1;
+  return pos;
+}
+
 __device__ __forceinline__ int annulus_of(long long p, int n, const double *edge2, int n_ann) {
   const long long x = (p % n) - n / 2, y = (p / n) - n / 2;
   const double rho2 = (double)(x * x + y * y);
@@ -118,10 +141,10 @@ __device__ __forceinline__ void hist_find(const uint32_t *hist, uint32_t krem, i
 // ---------------------------------------------------------------------------
 
 template <bool SMEM>
-__global__ void __launch_bounds__(256) collapse_kernel(const CollapseArgs a, int tcap) {
+__global__ void __launch_bounds__(256) collapse_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
   uint32_t *hist_all = csm;                 // [8][256]
-  uint32_t *keys_all = csm + 8 * 256;       // [8][tcap]   (SMEM only)
+  uint32_t *keys_all = csm + 8 * 256;       // [T][8] frame-major (SMEM only)
   const long long T = a.T;
   const long long NN = (long long)a.n * a.n;
   const long long p0 = (long long)blockIdx.x * 8;
@@ -129,21 +152,23 @@ __global__ void __launch_bounds__(256) collapse_kernel(const CollapseArgs a, int
 
   bool bad = false;
   if constexpr (SMEM) {
-    for (long long idx = threadIdx.x; idx < 8 * T; idx += 256) {
-      const int pw = (int)(idx & 7);
-      const long long t = idx >> 3;
-      const float v = a.in[t * NN + p0 + pw];
+    float *stage = reinterpret_cast<float *>(keys_all);
+    for (long long j = threadIdx.x; j < 2 * T; j += 256)
+      cp_async16(stage + 4 * j, a.in + (j >> 1) * NN + p0 + 4 * (j & 1));
+    cp_async_wait_all();
+    __syncthreads();
+    for (long long j = threadIdx.x; j < 8 * T; j += 256) {
+      const float v = stage[j];
       bad |= !isfinite(v);
-      keys_all[pw * tcap + t] = f2key(v);
+      keys_all[j] = f2key(v);
     }
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
     __syncthreads();
   }
   uint32_t *hist = hist_all + w * 256;
-  const uint32_t *keys = keys_all + w * tcap;
   const long long p = p0 + w;
   auto key_at = [&](long long t) -> uint32_t {
-    if constexpr (SMEM) return keys[t];
+    if constexpr (SMEM) return keys_all[t * 8 + w];
     else return f2key(a.in[t * NN + p]);
   };
 
@@ -231,6 +256,7 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   uint32_t *kB_all = kA_all + 8 * tcap;                        // [8][tcap]
   uint16_t *iA_all = reinterpret_cast<uint16_t *>(kB_all + 8 * tcap);   // [8][tcap]
   uint16_t *iB_all = iA_all + 8 * tcap;                                  // [8][tcap]
+  uint16_t *perm_s = iB_all + 8 * tcap;                                  // [tcap]
   __shared__ int ann_s[8];
 
   const int T = a.T;
@@ -240,18 +266,45 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   const int nw = tcap / 32;   // bitmap words per lane column
 
   if (lane == 0) ann_s[w] = annulus_of(p0 + w, a.n, a.edge2, a.n_ann);
+  for (int s = threadIdx.x; s < T; s += 256) perm_s[s] = (uint16_t)__ldg(&a.perm[s]);
   __syncthreads();
+  // a 4-pixel group whose annuli all have a band (or no annulus) belongs to
+  // adi_band_kernel, which runs after this kernel
+  bool banded[2];
+#pragma unroll
+  for (int g = 0; g < 2; g++) {
+    bool b = a.wmax > 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int an = ann_s[4 * g + q];
+      b &= (an < 0) || (__ldg(&a.band[4 * an + 2]) > 0);
+    }
+    banded[g] = b;
+  }
+  if (banded[0] && banded[1]) return;
   bool any = false;
 #pragma unroll
   for (int q = 0; q < 8; q++) any |= ann_s[q] >= 0;
   bool bad = false;
   if (any) {
-    for (int idx = threadIdx.x; idx < 8 * T; idx += 256) {
-      const int pw = idx & 7, s = idx >> 3;
-      const float v = a.in[(long long)a.perm[s] * NN + p0 + pw];
-      bad |= !isfinite(v);
-      kA_all[pw * tcap + s] = f2key(v);
-      iA_all[pw * tcap + s] = (uint16_t)s;
+    // all T x 8 values in flight at once: two 16-byte copies per frame into
+    // a frame-major staging area (the kB buffer), then keys into kA, rows
+    // per pixel
+    float *stage = reinterpret_cast<float *>(kB_all);
+    for (int j = threadIdx.x; j < 2 * T; j += 256) {
+      const int s = j >> 1, h = j & 1;
+      cp_async16(stage + s * 8 + 4 * h, a.in + (long long)perm_s[s] * NN + p0 + 4 * h);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (int pw = 0; pw < 8; pw++) {
+      for (int s = threadIdx.x; s < T; s += 256) {
+        const float v = stage[s * 8 + pw];
+        bad |= !isfinite(v);
+        kA_all[pw * tcap + s] = f2key(v);
+        iA_all[pw * tcap + s] = (uint16_t)s;
+      }
     }
   }
   if (bad) atomicOr(a.status, STATUS_NONFINITE);
@@ -259,8 +312,9 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
 
   const int ann = ann_s[w];
   const long long p = p0 + w;
+  if (banded[w >> 2]) return;
   if (ann < 0) {
-    for (int i = lane; i < T; i += 32) a.out[(long long)a.perm[i] * NN + p] = 0.0f;
+    for (int i = lane; i < T; i += 32) a.out[(long long)perm_s[i] * NN + p] = 0.0f;
     return;
   }
   uint32_t *hist = hist_all + w * 256;
@@ -378,15 +432,18 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
       const uint32_t word = bm[wd * 32 + c];
       const int pc = __popc(word);
       if (acc + pc > k) {
-        pos = wd * 32 + (int)__fns(word, 0, k - acc + 1);
+        pos = wd * 32 + nth_set(word, k - acc);
         break;
       }
       acc += pc;
     }
     int below = k;
     if (pos < 0) fail = true;
+    const int2 *LR2 = reinterpret_cast<const int2 *>(LR);
+    int2 nxt = __ldg(&LR2[i0]);
     for (int i = i0; i < i1 && !fail; i++) {
-      const int Ln = __ldg(&LR[2 * i]), Rn = __ldg(&LR[2 * i + 1]);
+      const int Ln = nxt.x, Rn = nxt.y;
+      if (i + 1 < i1) nxt = __ldg(&LR2[i + 1]);
       // toggle frames whose membership changes; keep `below` = set bits < pos
       for (int pass = 0; pass < 2; pass++) {
         const int s0 = pass == 0 ? min(L, Ln) : min(R, Rn);
@@ -431,7 +488,456 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
         med = (med + key2f(sk[hp])) * 0.5f;
       }
       const float v = key2f(sk[rk[i]]);
-      a.out[(long long)__ldg(&a.perm[i]) * NN + p] = v - med;
+      a.out[(long long)perm_s[i] * NN + p] = v - med;
+    }
+  }
+  if (fail) atomicOr(a.status, STATUS_INTERNAL);
+}
+
+// ---------------------------------------------------------------------------
+// Band path of the median PSF subtraction
+// ---------------------------------------------------------------------------
+
+constexpr uint16_t CODE_BELOW = 0xffff;
+constexpr uint16_t CODE_ABOVE = 0xfffe;
+constexpr int BAND_PPC = 4;   // pixels (warps) per CTA
+
+// In-register bitonic sort (ascending by key) of 32 E (key, tag) pairs held
+// as E consecutive elements per lane.  Equal keys keep their own tags.
+template <int E>
+__device__ __forceinline__ void bitonic_sort_warp(uint32_t (&k)[E], uint32_t (&x)[E], int lane) {
+  constexpr int P = 32 * E;
+#pragma unroll
+  for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= E) {
+        const int ls = stride / E;
+        const bool upper = (lane & ls) != 0;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+          const bool desc = ((lane * E + e) & size) != 0;
+          const uint32_t ok = __shfl_xor_sync(FULL, k[e], ls);
+          const uint32_t ox = __shfl_xor_sync(FULL, x[e], ls);
+          const bool take = (upper == desc) ? (ok < k[e]) : (ok > k[e]);
+          k[e] = take ? ok : k[e];
+          x[e] = take ? ox : x[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+          if (e & stride) continue;
+          const int e2 = e | stride;
+          const bool desc = ((lane * E + e) & size) != 0;
+          const bool sw = desc ? (k[e] < k[e2]) : (k[e] > k[e2]);
+          const uint32_t k0 = k[e], k1 = k[e2], x0 = x[e], x1 = x[e2];
+          k[e] = sw ? k1 : k0;
+          k[e2] = sw ? k0 : k1;
+          x[e] = sw ? x1 : x0;
+          x[e2] = sw ? x0 : x1;
+        }
+      }
+    }
+  }
+}
+
+// Sort the nb extracted band elements (bk keys, bidx frames) of one warp in
+// place and write code[frame] = sorted band position.
+template <int E>
+__device__ __forceinline__ void band_sort(uint32_t *bk, uint16_t *bidx, uint16_t *code, int nb, int lane) {
+  uint32_t k[E], x[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    const int j = lane * E + e;
+    k[e] = (j < nb) ? bk[j] : 0xffffffffu;
+    x[e] = (j < nb) ? (uint32_t)bidx[j] : 0xffffu;
+  }
+  __syncwarp();
+  bitonic_sort_warp<E>(k, x, lane);
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    const int j = lane * E + e;
+    if (j < nb) {
+      bk[j] = k[e];
+      bidx[j] = (uint16_t)x[e];
+      code[x[e]] = (uint16_t)j;
+    }
+  }
+  __syncwarp();
+}
+
+// Exact radix selects of the elements of full ranks r_lo <= r_hi among the T
+// keys keys[s * BAND_PPC] (s < T), sharing each histogram pass while both
+// prefixes agree: returns their keys and the numbers of smaller keys.
+// Histograms use fire-and-forget shared-memory reductions (no dependency
+// chain); digits equal in every key are skipped.
+__device__ __forceinline__ void band_select2(const uint32_t *keys, int T, uint32_t r_lo, uint32_t r_hi,
+                                             uint32_t varying, uint32_t andv, uint32_t *hlo, uint32_t *hhi,
+                                             int lane, uint32_t &Klo, uint32_t &clt_lo, uint32_t &Khi,
+                                             uint32_t &clt_hi) {
+  uint32_t plo = 0, phi = 0, pmask = 0, klo = r_lo, khi = r_hi;
+#pragma unroll 1
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 24 - 8 * pass;
+    if (((varying >> shift) & 255u) == 0) {
+      plo |= andv & (0xffu << shift);
+      phi |= andv & (0xffu << shift);
+      pmask |= 0xffu << shift;
+      continue;
+    }
+    const bool same = (plo == phi);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+      hlo[lane * 8 + b] = 0;
+      hhi[lane * 8 + b] = 0;
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int s = lane; s < T; s += 32) {
+      const uint32_t key = keys[s * BAND_PPC];
+      const uint32_t d = (key >> shift) & 255u;
+      const uint32_t km = key & pmask;
+      if (km == plo) atomicAdd(&hlo[d], 1u);
+      if (!same && km == phi) atomicAdd(&hhi[d], 1u);
+    }
+    __syncwarp();
+    uint32_t d, below, cnt;
+    hist_find(hlo, klo, lane, d, below, cnt);
+    plo |= d << shift;
+    klo -= below;
+    hist_find(same ? hlo : hhi, khi, lane, d, below, cnt);
+    phi |= d << shift;
+    khi -= below;
+    pmask |= 0xffu << shift;
+    __syncwarp();
+  }
+  Klo = plo;
+  clt_lo = r_lo - klo;
+  Khi = phi;
+  clt_hi = r_hi - khi;
+}
+
+__device__ __forceinline__ int band_next_set(const uint32_t *bm, int c, int x, int nw) {
+  int wd = x >> 5;
+  if (wd >= nw) return -1;
+  uint32_t word = bm[wd * 32 + c] & (0xffffffffu << (x & 31));
+  while (word == 0) {
+    if (++wd >= nw) return -1;
+    word = bm[wd * 32 + c];
+  }
+  return wd * 32 + __ffs(word) - 1;
+}
+
+// Shared-memory carve-up of adi_band_kernel (bytes), for tcap >= T and
+// bitmap width wmax words per lane.
+struct BandSmem {
+  size_t a, code, bk, bidx, hist, brank, perm, total;
+  __host__ __device__ BandSmem(int tcap, int wmax) {
+    const size_t bcm = 32 * (size_t)wmax;
+    const size_t keys_b = (size_t)BAND_PPC * tcap * 4;
+    const size_t late_b = (size_t)BAND_PPC * wmax * 32 * 4 + 2 * (size_t)tcap * 4;  // bitmaps + 2 staged gates
+    a = 0;
+    code = keys_b > late_b ? keys_b : late_b;
+    bk = code + (size_t)BAND_PPC * tcap * 2;
+    bidx = bk + (size_t)BAND_PPC * bcm * 4;
+    hist = bidx + (size_t)BAND_PPC * bcm * 2;
+    hist = (hist + 15) & ~(size_t)15;
+    brank = hist + (size_t)BAND_PPC * 512 * 4;
+    perm = brank + (size_t)BAND_PPC * 64 * 8;
+    total = perm + (size_t)tcap * 2;
+    total = (total + 15) & ~(size_t)15;
+  }
+};
+
+// Band path of the median PSF subtraction for 4-pixel groups whose largest
+// bitmap width W lies in (wmin, wmax].  Per pixel (one warp):
+//   1. keys at full ranks blo, bhi (two radix selects sharing passes);
+//   2. ordered extraction of the band (frames between the two, boundary ties
+//      split by frame order so that exactly bhi - blo + 1 frames are in it),
+//      codes BELOW / ABOVE for the others and a rank structure over BELOW;
+//   3. in-register bitonic sort of the band; code[frame] = band position;
+//   4. every lane builds its chunk-start membership bitmap over band
+//      positions and its count of BELOW frames in the reference set;
+//   5. every lane sweeps its chunk of queries: toggle the frames entering /
+//      leaving the set, walk a pointer to the t-th set bit, t = k - below.
+__global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArgs a, int tcap, int wmin) {
+  extern __shared__ __align__(16) unsigned char bsm_raw[];
+  const int T = a.T;
+  const int W_MAX = a.wmax;
+  const int BCM = 32 * W_MAX;
+  const BandSmem L(tcap, W_MAX);
+  uint32_t *keys = reinterpret_cast<uint32_t *>(bsm_raw + L.a);             // [T][4] (phases 0-2)
+  uint32_t *bm_all = reinterpret_cast<uint32_t *>(bsm_raw + L.a);           // [4][W_MAX][32] (phases 4-5)
+  uint32_t *gate_all = bm_all + BAND_PPC * W_MAX * 32;                      // [2][tcap] packed (L, R)
+  uint16_t *code_all = reinterpret_cast<uint16_t *>(bsm_raw + L.code);     // [4][tcap]
+  uint32_t *bk_all = reinterpret_cast<uint32_t *>(bsm_raw + L.bk);         // [4][BCM]
+  uint16_t *bidx_all = reinterpret_cast<uint16_t *>(bsm_raw + L.bidx);     // [4][BCM]
+  uint32_t *hist_all = reinterpret_cast<uint32_t *>(bsm_raw + L.hist);     // [4][512]
+  uint32_t *brank_all = reinterpret_cast<uint32_t *>(bsm_raw + L.brank);   // [4][64][2]
+  uint16_t *perm_s = reinterpret_cast<uint16_t *>(bsm_raw + L.perm);       // [tcap]
+  __shared__ int ann_s[BAND_PPC];
+  __shared__ int gate_ann[2];
+
+  const long long NN = (long long)a.n * a.n;
+  const long long p0 = (long long)blockIdx.x * BAND_PPC;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) ann_s[w] = annulus_of(p0 + w, a.n, a.edge2, a.n_ann);
+  __syncthreads();
+  bool mine = true, any = false;
+  int gw = 0;
+#pragma unroll
+  for (int q = 0; q < BAND_PPC; q++) {
+    const int an = ann_s[q];
+    const int Wq = an < 0 ? 0 : __ldg(&a.band[4 * an + 2]);
+    mine &= (an < 0) || (Wq > 0);
+    any |= an >= 0;
+    gw = max(gw, Wq);
+  }
+  // groups without annuli go to the first band launch
+  if (!mine || gw > W_MAX || (gw <= wmin && !(wmin == 0 && gw == 0))) return;
+  for (int s = threadIdx.x; s < T; s += 32 * BAND_PPC) perm_s[s] = (uint16_t)__ldg(&a.perm[s]);
+  __syncthreads();
+  const int ann = ann_s[w];
+  const long long p = p0 + w;
+  if (!any) {
+    for (int i = threadIdx.x; i < T * BAND_PPC; i += 32 * BAND_PPC)
+      a.out[(long long)perm_s[i / BAND_PPC] * NN + p0 + (i % BAND_PPC)] = 0.0f;
+    return;
+  }
+  // ---- 0. load: one 16-byte copy per frame (the 4 pixels), keys in place
+  {
+    float *stage = reinterpret_cast<float *>(keys);
+    for (int s = threadIdx.x; s < T; s += 32 * BAND_PPC)
+      cp_async16(stage + BAND_PPC * s, a.in + (long long)perm_s[s] * NN + p0);
+    cp_async_wait_all();
+    __syncthreads();
+    bool bad = false;
+    for (int j = threadIdx.x; j < T * BAND_PPC; j += 32 * BAND_PPC) {
+      const float v = stage[j];
+      bad |= !isfinite(v);
+      keys[j] = f2key(v);
+    }
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    __syncthreads();
+  }
+  const int blo = ann >= 0 ? __ldg(&a.band[4 * ann]) : 0;
+  const int bhi = ann >= 0 ? __ldg(&a.band[4 * ann + 1]) : 0;
+  const int W = ann >= 0 ? __ldg(&a.band[4 * ann + 2]) : 0;
+  const uint32_t *kw = keys + w;                 // key of frame s: kw[s * 4]
+  uint32_t *hist = hist_all + w * 512;
+  uint32_t *bk = bk_all + w * BCM;
+  uint16_t *code = code_all + w * tcap;
+  uint16_t *bidx = bidx_all + w * BCM;
+  uint32_t *brank = brank_all + w * 128;         // [64] BELOW masks, [64] BELOW counts before each round
+  bool fail = false;
+  int nb = 0, nbelow = 0;
+
+  if (ann >= 0) {
+    // ---- 1. exact keys at full ranks blo and bhi ------------------------
+    uint32_t orv = 0, andv = 0xffffffffu;
+    for (int s = lane; s < T; s += 32) {
+      orv |= kw[s * BAND_PPC];
+      andv &= kw[s * BAND_PPC];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      orv |= __shfl_xor_sync(FULL, orv, o);
+      andv &= __shfl_xor_sync(FULL, andv, o);
+    }
+    uint32_t Klo, Khi, clt_lo, clt_hi;
+    band_select2(kw, T, (uint32_t)blo, (uint32_t)bhi, orv ^ andv, andv, hist, hist + 256, lane, Klo, clt_lo,
+                 Khi, clt_hi);
+    // ---- 2. ordered extraction -------------------------------------------
+    const int need_lo = blo - (int)clt_lo;
+    const int lim_hi = bhi + 1 - (int)clt_hi;
+    const unsigned lt = (1u << lane) - 1u;
+    int tlo = 0, thi = 0;
+    for (int base = 0; base < T; base += 32) {
+      const int s = base + lane;
+      const bool valid = s < T;
+      const uint32_t key = valid ? kw[s * BAND_PPC] : 0u;
+      const bool eqlo = valid && key == Klo, eqhi = valid && key == Khi;
+      const unsigned mlo = __ballot_sync(FULL, eqlo), mhi = __ballot_sync(FULL, eqhi);
+      const int ilo = tlo + __popc(mlo & lt), ihi = thi + __popc(mhi & lt);
+      const bool below = valid && (key < Klo || (eqlo && ilo < need_lo));
+      const bool above = valid && !below && (key > Khi || (eqhi && ihi >= lim_hi));
+      const bool inb = valid && !below && !above;
+      const unsigned mb = __ballot_sync(FULL, inb), mbl = __ballot_sync(FULL, below);
+      if (inb) {
+        const int j = nb + __popc(mb & lt);
+        if (j < BCM) {
+          bk[j] = key;
+          bidx[j] = (uint16_t)s;
+        }
+      } else if (valid) {
+        code[s] = below ? CODE_BELOW : CODE_ABOVE;
+      }
+      if (lane == 0) {
+        brank[base >> 5] = mbl;
+        brank[64 + (base >> 5)] = (uint32_t)nbelow;
+      }
+      tlo += __popc(mlo);
+      thi += __popc(mhi);
+      nb += __popc(mb);
+      nbelow += __popc(mbl);
+    }
+    if (nb != bhi - blo + 1 || nb > 32 * W) fail = true;
+    __syncwarp();
+    // ---- 3. sort the band; codes of band frames = sorted positions -------
+    if (!fail) {
+      switch (W) {
+        case 1: band_sort<1>(bk, bidx, code, nb, lane); break;
+        case 2: band_sort<2>(bk, bidx, code, nb, lane); break;
+        case 4: band_sort<4>(bk, bidx, code, nb, lane); break;
+        case 8: band_sort<8>(bk, bidx, code, nb, lane); break;
+        case 16: band_sort<16>(bk, bidx, code, nb, lane); break;
+        default: band_sort<32>(bk, bidx, code, nb, lane); break;
+      }
+    }
+  }
+  // keys are dead from here on: their space holds the bitmaps and the gates
+  __syncthreads();
+  if (threadIdx.x < 2) gate_ann[threadIdx.x] = -1;
+  __syncthreads();
+  if (lane == 0 && ann >= 0) {
+    // the (at most two) annuli of this group get their gate staged once
+    if (atomicCAS(&gate_ann[0], -1, ann) != -1 && gate_ann[0] != ann) atomicCAS(&gate_ann[1], -1, ann);
+  }
+  __syncthreads();
+  for (int g = 0; g < 2; g++) {
+    const int an = gate_ann[g];
+    if (an < 0) continue;
+    const int2 *lr2 = reinterpret_cast<const int2 *>(a.lr + (size_t)an * T * 2);
+    uint32_t *gt = gate_all + g * tcap;
+    for (int s = threadIdx.x; s < T; s += 32 * BAND_PPC) {
+      const int2 v = __ldg(&lr2[s]);
+      gt[s] = (uint32_t)v.x | ((uint32_t)v.y << 16);
+    }
+  }
+  __syncthreads();
+  if (ann < 0) {
+    for (int i = lane; i < T; i += 32) a.out[(long long)perm_s[i] * NN + p] = 0.0f;
+    return;
+  }
+  if (fail) {
+    if (lane == 0) atomicOr(a.status, STATUS_INTERNAL);
+    return;
+  }
+  // gate of this pixel's annulus: staged copy, or global memory for a third
+  // annulus inside one 4-pixel group
+  const uint32_t *gate = gate_ann[0] == ann ? gate_all : (gate_ann[1] == ann ? gate_all + tcap : nullptr);
+  const int2 *gate_g = reinterpret_cast<const int2 *>(a.lr + (size_t)ann * T * 2);
+  auto gate_at = [&](int i) -> uint32_t {
+    if (gate) return gate[i];
+    const int2 v = __ldg(&gate_g[i]);
+    return (uint32_t)v.x | ((uint32_t)v.y << 16);
+  };
+  uint32_t *bm = bm_all + w * W_MAX * 32;
+  auto below_before = [&](int s) -> int {      // BELOW frames with sorted position < s
+    if (s >= T) return nbelow;
+    const int r = s >> 5;
+    return (int)brank[64 + r] + __popc(brank[r] & ((1u << (s & 31)) - 1u));
+  };
+
+  // ---- 4. chunk-start bitmap and BELOW count of each lane --------------
+  const int C = (T + 31) / 32;
+  const int c = lane;
+  const int i0 = c * C;
+  const int i1 = min(T, i0 + C);
+  int cb = 0;
+  if (i0 < T) {
+    const uint32_t g0 = gate_at(i0);
+    const int L0 = (int)(g0 & 0xffffu), R0 = (int)(g0 >> 16);
+    for (int wd = 0; wd < W; wd++) {
+      uint32_t word = 0;
+#pragma unroll 8
+      for (int b = 0; b < 32; b++) {
+        const int pb = wd * 32 + b;
+        const int f = bidx[pb];                       // same address in every lane
+        word |= (pb < nb && (f < L0 || f >= R0)) ? (1u << b) : 0u;
+      }
+      bm[wd * 32 + c] = word;
+    }
+    cb = below_before(L0) + (nbelow - below_before(R0));
+  }
+  __syncwarp();
+
+  // ---- 5. per-lane sweep ------------------------------------------------
+  // State: word wi of the bitmap column holds the t-th set bit, base = set
+  // bits in words < wi.  Gates of band annuli are monotone (host check):
+  // frames [L, L') enter the reference set, frames [R, R') leave it.
+  if (i0 < T) {
+    const uint32_t g0 = gate_at(i0);
+    int Lc = (int)(g0 & 0xffffu), Rc = (int)(g0 >> 16);
+    int wi = 0, base = 0;
+    const float *src = a.in + p;
+    float v0 = src[(long long)perm_s[i0] * NN];
+    float v1 = (i0 + 1 < i1) ? src[(long long)perm_s[i0 + 1] * NN] : 0.f;
+    float v2 = (i0 + 2 < i1) ? src[(long long)perm_s[i0 + 2] * NN] : 0.f;
+    for (int i = i0; i < i1; i++) {
+      const float v = v0;
+      v0 = v1;
+      v1 = v2;
+      if (i + 3 < i1) v2 = src[(long long)perm_s[i + 3] * NN];
+      const uint32_t gi = gate_at(i);
+      const int Ln = (int)(gi & 0xffffu), Rn = (int)(gi >> 16);
+      for (int s = Lc; s < Ln; s++) {            // entering
+        const uint16_t cd = code[s];
+        if (cd < CODE_ABOVE) {
+          const int wq = cd >> 5;
+          bm[wq * 32 + c] ^= 1u << (cd & 31);
+          base += (wq < wi) ? 1 : 0;
+        } else {
+          cb += (cd == CODE_BELOW) ? 1 : 0;
+        }
+      }
+      for (int s = Rc; s < Rn; s++) {            // leaving
+        const uint16_t cd = code[s];
+        if (cd < CODE_ABOVE) {
+          const int wq = cd >> 5;
+          bm[wq * 32 + c] ^= 1u << (cd & 31);
+          base -= (wq < wi) ? 1 : 0;
+        } else {
+          cb -= (cd == CODE_BELOW) ? 1 : 0;
+        }
+      }
+      Lc = Ln;
+      Rc = Rn;
+      const int nset = Lc + (T - Rc);
+      const int t = ((nset - 1) >> 1) - cb;
+      uint32_t wd = bm[wi * 32 + c];
+      int pc = __popc(wd);
+      while (t < base && wi > 0) {
+        wi--;
+        wd = bm[wi * 32 + c];
+        pc = __popc(wd);
+        base -= pc;
+      }
+      while (t >= base + pc && wi + 1 < W) {
+        base += pc;
+        wi++;
+        wd = bm[wi * 32 + c];
+        pc = __popc(wd);
+      }
+      if (t < base || t >= base + pc) {
+        fail = true;
+        break;
+      }
+      float med = key2f(bk[wi * 32 + nth_set(wd, t - base)]);
+      if ((nset & 1) == 0) {
+        int p2;
+        if (t + 1 < base + pc) {
+          p2 = wi * 32 + nth_set(wd, t - base + 1);
+        } else {
+          p2 = band_next_set(bm, c, (wi + 1) * 32, W);
+          if (p2 < 0) {
+            fail = true;
+            break;
+          }
+        }
+        med = (med + key2f(bk[p2])) * 0.5f;
+      }
+      a.out[(long long)perm_s[i] * NN + p] = v - med;
     }
   }
   if (fail) atomicOr(a.status, STATUS_INTERNAL);
@@ -445,19 +951,20 @@ int pow2_at_least(long long x, int lo) {
 
 }  // namespace
 
+cudaError_t launch_adi_general(const AdiArgs &a, cudaStream_t st, int tcap);
+
 cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
   const long long NN = (long long)a.n * a.n;
   const unsigned grid = (unsigned)(NN / 8);
   if (a.T <= 4096) {
-    const int tcap = pow2_at_least(a.T, 32);
-    const size_t smem = (size_t)(8 * 256 + 8 * tcap) * sizeof(uint32_t);
+    const size_t smem = (size_t)(8 * 256 + 8 * a.T) * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(collapse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    collapse_kernel<true><<<grid, 256, smem, st>>>(a, tcap);
+    collapse_kernel<true><<<grid, 256, smem, st>>>(a);
   } else {
     const size_t smem = (size_t)(8 * 256) * sizeof(uint32_t);
-    collapse_kernel<false><<<grid, 256, smem, st>>>(a, 0);
+    collapse_kernel<false><<<grid, 256, smem, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -465,7 +972,32 @@ cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
 cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st) {
   const long long NN = (long long)a.n * a.n;
   const int tcap = pow2_at_least(a.T, 32);
-  const size_t smem = (size_t)8 * 256 * sizeof(uint32_t) + (size_t)8 * tcap * (2 * sizeof(uint32_t) + 2 * sizeof(uint16_t));
+  // general kernel first: it reads every pixel of its groups and writes only
+  // its own; the band launches then own disjoint 4-pixel groups
+  cudaError_t e = launch_adi_general(a, st, tcap);
+  if (e != cudaSuccess || a.wmax == 0) return e;
+  // band launches: groups whose widest bitmap is <= 16 words, then wider ones,
+  // each with shared memory sized for its widest class
+  const int split = a.wmax < 16 ? a.wmax : 16;
+  const int ranges[2][2] = {{0, split}, {split, a.wmax}};
+  for (int r = 0; r < 2; r++) {
+    if (ranges[r][1] <= ranges[r][0] && r == 1) break;
+    AdiArgs b = a;
+    b.wmax = ranges[r][1];
+    const BandSmem L(tcap, b.wmax);
+    e = cudaFuncSetAttribute(adi_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    adi_band_kernel<<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(b, tcap, ranges[r][0]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_adi_general(const AdiArgs &a, cudaStream_t st, int tcap) {
+  const long long NN = (long long)a.n * a.n;
+  const size_t smem = (size_t)8 * 256 * sizeof(uint32_t) +
+                      (size_t)8 * tcap * (2 * sizeof(uint32_t) + 2 * sizeof(uint16_t)) + (size_t)tcap * sizeof(uint16_t);
   cudaError_t e = cudaFuncSetAttribute(adi_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   adi_median_kernel<<<(unsigned)(NN / 8), 256, smem, st>>>(a, tcap);

@@ -280,3 +280,30 @@ def test_errors(g):
     # the context stays usable after errors
     out = g.graphic_shift(f, [0.5, 0.5], [0.0, 0.0])
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.parametrize("T,levels", [(300, 3), (700, 7), (1500, 50), (2048, 2)])
+def test_adi_subtract_ties_bit_exact(g, T, levels):
+    """Quantised values: many keys equal to the band's boundary keys, which
+    the band path has to split by frame order; results must stay exact."""
+    n = 64
+    rng = np.random.default_rng(T + levels)
+    c = rng.integers(0, levels, (T, n, n)).astype(np.float32) * 0.5 - 1.0
+    pa = np.linspace(-60, 60, T) + rng.uniform(-0.01, 0.01, T)
+    edges = [1.0, 6.0, 14.0, 30.0, 46.0]
+    out = g.graphic_adi_subtract(dev(c), pa, 4.0, 1.5, edges).cpu().numpy()
+    pix = np.random.default_rng(1).choice(n * n, 40, replace=False)
+    pix = np.concatenate([pix, [n * n // 2 + n // 2 + 3, (n // 2 + 20) * n + n // 2]])
+    ref = oracle.adi_subtract(c, pa, 4.0, 1.5, edges, pixels=pix)
+    assert np.array_equal(out.reshape(T, n * n)[:, pix].T, ref)
+
+
+def test_adi_subtract_thin_annuli_bit_exact(g):
+    """Annuli one pixel wide: a group of 4 neighbouring pixels spans up to
+    four annuli (the band kernel stages two gates and reads the others)."""
+    T, n = 120, 64
+    c, pa = _adi_case(T, n, seed=3)
+    edges = [6.0, 7.0, 8.0, 9.0, 10.0, 11.0, 12.0, 30.0]
+    out = g.graphic_adi_subtract(dev(c), pa, 4.0, 1.5, edges).cpu().numpy()
+    ref = oracle.adi_subtract(c, pa, 4.0, 1.5, edges)
+    assert np.array_equal(out, ref)
