@@ -198,16 +198,29 @@ __device__ __forceinline__ void load_smem(float2 (&v)[16], int j, const float2 *
   for (int m = 0; m < 16; m++) v[m] = src[padi(j + m * (M / 16))];
 }
 
+// Barrier among the M/16 threads of one line pair: a named barrier (id 1 + p)
+// when the pair spans several warps, otherwise the warp's own barrier.
+template <int M>
+__device__ __forceinline__ void pair_sync(int p) {
+  constexpr int TPL = M / 16;
+  if constexpr (TPL > 32) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + p), "r"(TPL) : "memory");
+  } else {
+    __syncwarp();
+  }
+}
+
 // Stages 1.. of a forward transform from smem buffer `a` (ping-pong with
 // `b`); stage 0 has already been computed and stored into `a`.  Returns the
 // buffer holding the natural-order result (all stages but the last), or,
-// when LAST_TO_REGS, leaves the last stage's outputs in v.
+// when LAST_TO_REGS, leaves the last stage's outputs in v.  Only the
+// threads of line pair p take part.
 template <int M, bool LAST_TO_REGS>
-__device__ __forceinline__ float2 *run_stages(float2 (&v)[16], int j, float2 *a, float2 *b,
+__device__ __forceinline__ float2 *run_stages(float2 (&v)[16], int j, int p, float2 *a, float2 *b,
                                               const float2 *__restrict__ tw) {
   constexpr int S = NumStages<M>::value;
   // stage 1
-  __syncthreads();
+  pair_sync<M>(p);
   load_smem<M>(v, j, a);
   stage_compute<M, Radix<M, 1>::value, 16>(v, j, tw);
   if constexpr (S == 2) {
@@ -218,7 +231,7 @@ __device__ __forceinline__ float2 *run_stages(float2 (&v)[16], int j, float2 *a,
     return nullptr;
   } else {
     stage_store_smem<M, Radix<M, 1>::value, 16>(v, j, b);
-    __syncthreads();
+    pair_sync<M>(p);
     load_smem<M>(v, j, b);
     stage_compute<M, Radix<M, 2>::value, 256>(v, j, tw);
     if constexpr (!LAST_TO_REGS) {
@@ -383,33 +396,35 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
 
   // ---- forward transform, stage 0 straight from global memory ----------
   float2 v[16];
+  {
 #pragma unroll
-  for (int m = 0; m < 16; m++) {
-    const int pos = j + m * (M / 16);
-    float2 z = make_float2(0.f, 0.f);
-    if (m * (M / 16) < NIN) {   // compile-time pruning of the zero half
-      if constexpr (KIND == SHIFT_X) {
-        z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
-      } else if constexpr (KIND == SHIFT_Y) {
-        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
-      } else if constexpr (KIND == ROT_P1) {
-        z = load_rot90_pair(fin, N, q, line0, pos);
-      } else if constexpr (KIND == ROT_P2) {
-        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
-      } else {
-        z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+    for (int m = 0; m < 16; m++) {
+      const int pos = j + m * (M / 16);
+      float2 z = make_float2(0.f, 0.f);
+      if (m * (M / 16) < NIN) {   // compile-time pruning of the zero half
+        if constexpr (KIND == SHIFT_X) {
+          z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
+        } else if constexpr (KIND == SHIFT_Y) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+        } else if constexpr (KIND == ROT_P1) {
+          z = load_rot90_pair(fin, N, q, line0, pos);
+        } else if constexpr (KIND == ROT_P2) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
+        } else {
+          z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+        }
+        if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
       }
-      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+      v[m] = z;
     }
-    v[m] = z;
-  }
-  if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
-    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
+      if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    }
   }
   stage_compute<M, 16, 1>(v, j, tw);
   stage_store_smem<M, 16, 1>(v, j, bufA);
-  float2 *spec = run_stages<M, false>(v, j, bufA, bufB, tw);
-  __syncthreads();
+  float2 *spec = run_stages<M, false>(v, j, p, bufA, bufB, tw);
+  pair_sync<M>(p);
 
   // ---- middle: phasors (and separation of the two real spectra) ---------
   {
@@ -450,38 +465,309 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
       spec[padi(M / 2)] = make_float2(z.x * la.cnyq * inv_m, -z.y * lb.cnyq * inv_m);
     }
   }
-  __syncthreads();
+  pair_sync<M>(p);
 
   // ---- inverse via forward stages on conj(V)/m --------------------------
   float2 *other = (spec == bufA) ? bufB : bufA;
   load_smem<M>(v, j, spec);
   stage_compute<M, 16, 1>(v, j, tw);
   stage_store_smem<M, 16, 1>(v, j, other);
-  run_stages<M, true>(v, j, other, spec, tw);
+  run_stages<M, true>(v, j, p, other, spec, tw);
 
   // ---- store: slot (u, r) -> position vt + r M/R; y = conj(result) -------
   constexpr int RL = LastStage<M>::R;
   constexpr int UL = LastStage<M>::U;
+  {
 #pragma unroll
-  for (int u = 0; u < UL; u++) {
+    for (int u = 0; u < UL; u++) {
 #pragma unroll
-    for (int r = 0; r < RL; r++) {
-      const int pos = j + u * (M / 16) + r * (M / RL);
-      if (r * (M / RL) < NOUT) {
-        const float2 y = v[u + UL * r];
-        if constexpr (KIND == SHIFT_Y) {
-          *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = make_float2(y.x, -y.y);
-        } else if constexpr (KIND == ROT_P2) {
-          *reinterpret_cast<float2 *>(fout + (size_t)pos * M + line0) = make_float2(y.x, -y.y);
-        } else {
-          const int rs = (KIND == ROT_P1) ? M : N;
-          fout[(size_t)line0 * rs + pos] = y.x;
-          fout[(size_t)(line0 + 1) * rs + pos] = -y.y;
+      for (int r = 0; r < RL; r++) {
+        const int pos = j + u * (M / 16) + r * (M / RL);
+        if (r * (M / RL) < NOUT) {
+          const float2 y = v[u + UL * r];
+          if constexpr (KIND == SHIFT_Y) {
+            *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = make_float2(y.x, -y.y);
+          } else if constexpr (KIND == ROT_P2) {
+            *reinterpret_cast<float2 *>(fout + (size_t)pos * M + line0) = make_float2(y.x, -y.y);
+          } else {
+            const int rs = (KIND == ROT_P1) ? M : N;
+            fout[(size_t)line0 * rs + pos] = y.x;
+            fout[(size_t)(line0 + 1) * rs + pos] = -y.y;
+          }
         }
       }
     }
   }
   (void)NLINES;
+}
+
+// ---------------------------------------------------------------------------
+// m = 1024: one warp per line pair, 32 complex values per thread.
+// Forward FFT = two Stockham stages of radix 32 (one shared-memory exchange),
+// the thread holding bins k = lane + 32 r afterwards; the pair separation
+// reads the conjugate-partner bin through shared memory; the inverse reuses
+// the same two stages on conj(V)/m.
+// ---------------------------------------------------------------------------
+
+// cos(2 pi m / 32) for m = 0..8 (the others follow by symmetry).
+#define G_C32_0 1.0f
+#define G_C32_1 0.98078528040323044913f
+#define G_C32_2 0.92387953251128675613f
+#define G_C32_3 0.83146961230254523708f
+#define G_C32_4 0.70710678118654752440f
+#define G_C32_5 0.55557023301960222474f
+#define G_C32_6 0.38268343236508977173f
+#define G_C32_7 0.19509032201612826785f
+#define G_C32_8 0.0f
+
+__host__ __device__ constexpr float c32_base(int m) {
+  return m == 0 ? G_C32_0 : m == 1 ? G_C32_1 : m == 2 ? G_C32_2 : m == 3 ? G_C32_3 : m == 4 ? G_C32_4
+       : m == 5 ? G_C32_5 : m == 6 ? G_C32_6 : m == 7 ? G_C32_7 : G_C32_8;
+}
+// cos and sin of 2 pi m / 32 for any m, from the first octant
+__host__ __device__ constexpr float c32(int m) {
+  return (m & 31) <= 8 ? c32_base(m & 31)
+       : (m & 31) <= 16 ? -c32_base(16 - (m & 31))
+       : (m & 31) <= 24 ? -c32_base((m & 31) - 16) : c32_base(32 - (m & 31));
+}
+__host__ __device__ constexpr float s32(int m) {
+  return (m & 31) <= 8 ? c32_base(8 - (m & 31))
+       : (m & 31) <= 16 ? c32_base((m & 31) - 8)
+       : (m & 31) <= 24 ? -c32_base(24 - (m & 31)) : -c32_base((m & 31) - 24);
+}
+
+template <int J>
+__device__ __forceinline__ float2 mul_w32(float2 a) {
+  constexpr int j = J & 31;
+  if constexpr (j == 0) return a;
+  else if constexpr (j == 8) return make_float2(a.y, -a.x);
+  else if constexpr (j == 16) return make_float2(-a.x, -a.y);
+  else if constexpr (j == 24) return make_float2(-a.y, a.x);
+  else {
+    constexpr float c = c32(j), s = s32(j);
+    return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+  }
+}
+
+// In-place forward DFT of size 32, natural order out: n = 8 n1 + n2,
+// k = k1 + 4 k2 (inner DFT4 over n1, twiddle W32^(n2 k1), outer DFT8 over n2).
+template <int K1>
+__device__ __forceinline__ void w32_row(float2 (&a)[32]) {
+  a[8 * K1 + 1] = mul_w32<1 * K1>(a[8 * K1 + 1]);
+  a[8 * K1 + 2] = mul_w32<2 * K1>(a[8 * K1 + 2]);
+  a[8 * K1 + 3] = mul_w32<3 * K1>(a[8 * K1 + 3]);
+  a[8 * K1 + 4] = mul_w32<4 * K1>(a[8 * K1 + 4]);
+  a[8 * K1 + 5] = mul_w32<5 * K1>(a[8 * K1 + 5]);
+  a[8 * K1 + 6] = mul_w32<6 * K1>(a[8 * K1 + 6]);
+  a[8 * K1 + 7] = mul_w32<7 * K1>(a[8 * K1 + 7]);
+}
+
+__device__ __forceinline__ void dft32(float2 (&a)[32]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 8; n2++) dft4(a[n2], a[n2 + 8], a[n2 + 16], a[n2 + 24]);
+  w32_row<1>(a);
+  w32_row<2>(a);
+  w32_row<3>(a);
+  float2 t[32];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; k1++) {
+    float2 b[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; n2++) b[n2] = a[8 * k1 + n2];
+    dft<8>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; k2++) t[k1 + 4 * k2] = b[k2];
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i++) a[i] = t[i];
+}
+
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+// Two radix-32 Stockham stages over the 1024-point line held as v[m] =
+// element lane + 32 m: after the call v[r] = X[lane + 32 r].  buf: the warp's
+// exchange buffer (1024 + 32 entries).
+__device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *buf,
+                                             const float2 *__restrict__ tw) {
+  dft32(v);
+#pragma unroll
+  for (int r = 0; r < 32; r++) buf[pad32(32 * lane + r)] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < 32; m++) v[m] = buf[pad32(lane + 32 * m)];
+#pragma unroll
+  for (int r = 1; r < 32; r++) v[r] = cmul(v[r], __ldg(&tw[r * lane]));
+  dft32(v);
+  __syncwarp();
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
+  constexpr int M = 1024, N = 512, PPC = 4;
+  constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
+  constexpr int NIN = (KIND == ROT_P3) ? M : N;
+  constexpr int NOUT = (KIND == ROT_P1) ? M : N;
+  __shared__ float2 sbuf[PPC][M + M / 32];
+  __shared__ LineParam lp[PPC][2];
+  __shared__ int ident_s;
+
+  const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
+  const long long f = blockIdx.y;
+  const int line0 = 2 * (blockIdx.x * PPC + p);
+  const float *__restrict__ fin = a.in + f * a.in_fstride;
+  float *__restrict__ fout = a.out + f * a.out_fstride;
+  const float2 *__restrict__ tw = d_twiddle + tw_off(M);
+  float2 *buf = sbuf[p];
+  const int q = (KIND == ROT_P1) ? (a.q[f] & 3) : 0;
+
+  if (threadIdx.x == 0) {
+    bool id;
+    if constexpr (KIND == SHIFT_X) id = (a.p0[f] == 0.0);
+    else if constexpr (KIND == SHIFT_Y) id = (a.p1[f] == 0.0);
+    else id = (a.p0[f] == 0.0 && a.p1[f] == 0.0);
+    ident_s = id ? 1 : 0;
+  }
+  if (lane < 2 && (!SAME_D || lane == 0)) make_param(lp[p][lane], line_shift<KIND>(a, f, line0 + lane, N), M);
+  __syncthreads();
+
+  bool bad = false;
+  if (ident_s) {
+    if constexpr (KIND == ROT_P2) return;
+    for (int pos = lane; pos < NOUT; pos += 32) {
+      float2 z = make_float2(0.f, 0.f);
+      if (pos < NIN) {
+        if constexpr (KIND == SHIFT_X || KIND == ROT_P3) {
+          const int rs = (KIND == ROT_P3) ? M : N;
+          z = make_float2(fin[(size_t)line0 * rs + pos], fin[(size_t)(line0 + 1) * rs + pos]);
+        } else if constexpr (KIND == SHIFT_Y) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+        } else if constexpr (KIND == ROT_P1) {
+          z = load_rot90_pair(fin, N, q, line0, pos);
+        }
+      }
+      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+      if constexpr (KIND == SHIFT_Y) {
+        *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = z;
+      } else {
+        const int rs = (KIND == ROT_P1) ? M : N;
+        fout[(size_t)line0 * rs + pos] = z.x;
+        fout[(size_t)(line0 + 1) * rs + pos] = z.y;
+      }
+    }
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    return;
+  }
+
+  // ---- load: v[m] = element lane + 32 m of the line pair -----------------
+  float2 v[32];
+#pragma unroll
+  for (int m = 0; m < 32; m++) {
+    const int pos = lane + 32 * m;
+    float2 z = make_float2(0.f, 0.f);
+    if (32 * m < NIN) {
+      if constexpr (KIND == SHIFT_X) {
+        z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
+      } else if constexpr (KIND == SHIFT_Y) {
+        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+      } else if constexpr (KIND == ROT_P1) {
+        z = load_rot90_pair(fin, N, q, line0, pos);
+      } else if constexpr (KIND == ROT_P2) {
+        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
+      } else {
+        z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+      }
+      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+    }
+    v[m] = z;
+  }
+  if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
+    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+  }
+  fft1024_warp(v, lane, buf, tw);
+
+  // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
+  if constexpr (!SAME_D) {
+#pragma unroll
+    for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
+    __syncwarp();
+  }
+  const LineParam &la = lp[p][0];
+  const LineParam &lb = lp[p][SAME_D ? 0 : 1];
+  const float inv_m = 1.0f / (float)M;
+  // phasors H_k = exp(-i 2 pi ks delta), ks the signed bin: exact anchors at
+  // r = 0, 8, 16, 24, a product with exp(-i 2 pi 32 delta) in between
+  const float2 sa = phase_at(la, 32);
+  const float2 sb = SAME_D ? sa : phase_at(lb, 32);
+  float2 ha, hb;
+#pragma unroll
+  for (int r = 0; r < 32; r++) {
+    const int k = lane + 32 * r;
+    if ((r & 7) == 0) {
+      const int ks = (r < 16) ? k : k - M;
+      ha = phase_at(la, ks);
+      hb = SAME_D ? ha : phase_at(lb, ks);
+    } else {
+      ha = cmul(ha, sa);
+      hb = SAME_D ? ha : cmul(hb, sb);
+    }
+    float2 ua = ha, ub = hb;
+    if (r == 16 && lane == 0) {   // Nyquist bin
+      ua = make_float2(la.cnyq, 0.f);
+      ub = make_float2(lb.cnyq, 0.f);
+    }
+    const float2 z = v[r];
+    float2 vk;
+    if constexpr (SAME_D) {
+      vk = cmul(z, ua);
+    } else {
+      const float2 zm = buf[pad32((M - k) & (M - 1))];
+      const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+      const float2 P = cmul(A, ua), Q = cmul(B, ub);
+      vk = make_float2(P.x - Q.y, P.y + Q.x);
+    }
+    v[r] = make_float2(vk.x * inv_m, -vk.y * inv_m);   // conj(V) / m
+  }
+  __syncwarp();
+
+  // ---- inverse: the same stages on conj(V)/m; y = conj(result) ------------
+  fft1024_warp(v, lane, buf, tw);
+#pragma unroll
+  for (int r = 0; r < 32; r++) {
+    const int pos = lane + 32 * r;
+    if (32 * r < NOUT) {
+      const float2 y = v[r];
+      if constexpr (KIND == SHIFT_Y) {
+        *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = make_float2(y.x, -y.y);
+      } else if constexpr (KIND == ROT_P2) {
+        *reinterpret_cast<float2 *>(fout + (size_t)pos * M + line0) = make_float2(y.x, -y.y);
+      } else {
+        const int rs = (KIND == ROT_P1) ? M : N;
+        fout[(size_t)line0 * rs + pos] = y.x;
+        fout[(size_t)(line0 + 1) * rs + pos] = -y.y;
+      }
+    }
+  }
+}
+
+template <int KIND>
+cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
+  constexpr int M = 1024, N = 512, PPC = 4;
+  constexpr int NLINES = (KIND == ROT_P2) ? M : N;
+  for (long long f0 = 0; f0 < n_frames; f0 += 65535) {
+    const long long nf = (n_frames - f0 < 65535) ? (n_frames - f0) : 65535;
+    LineArgs b = a;
+    b.in = a.in + f0 * a.in_fstride;
+    b.out = a.out + f0 * a.out_fstride;
+    b.p0 = a.p0 ? a.p0 + f0 : nullptr;
+    b.p1 = a.p1 ? a.p1 + f0 : nullptr;
+    b.q = a.q ? a.q + f0 : nullptr;
+    dim3 grid(NLINES / (2 * PPC), (unsigned)nf);
+    line_pass_w32<KIND><<<grid, 32 * PPC, 0, st>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <int M>
@@ -554,7 +840,15 @@ cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frame
     case 64: return launch_m<128>(kind, a, n_frames, st);
     case 128: return launch_m<256>(kind, a, n_frames, st);
     case 256: return launch_m<512>(kind, a, n_frames, st);
-    case 512: return launch_m<1024>(kind, a, n_frames, st);
+    case 512:
+      switch (kind) {
+        case SHIFT_X: return launch_w32<SHIFT_X>(a, n_frames, st);
+        case SHIFT_Y: return launch_w32<SHIFT_Y>(a, n_frames, st);
+        case ROT_P1: return launch_w32<ROT_P1>(a, n_frames, st);
+        case ROT_P2: return launch_w32<ROT_P2>(a, n_frames, st);
+        case ROT_P3: return launch_w32<ROT_P3>(a, n_frames, st);
+      }
+      return cudaErrorInvalidValue;
     case 1024: return launch_m<2048>(kind, a, n_frames, st);
   }
   return cudaErrorInvalidValue;

@@ -628,6 +628,20 @@ __device__ __forceinline__ int band_next_set(const uint32_t *bm, int c, int x, i
   return wd * 32 + __ffs(word) - 1;
 }
 
+// Frame s enters (sign +1) or leaves (sign -1) the reference set of lane c:
+// flip its band bit (base counts set bits in words before wi) or count it
+// among the BELOW frames.  Branch-free; an inactive call changes nothing.
+__device__ __forceinline__ void band_toggle(const uint16_t *code, uint32_t *bm, int c, int s, bool active, int sign,
+                                            int wi, int &base, int &cb) {
+  const uint16_t cd = active ? code[s] : CODE_ABOVE;
+  const bool isb = cd < CODE_ABOVE;
+  const int wq = isb ? (cd >> 5) : 0;
+  const uint32_t bit = isb ? (1u << (cd & 31)) : 0u;
+  bm[wq * 32 + c] ^= bit;
+  base += (isb && wq < wi) ? sign : 0;
+  cb += (cd == CODE_BELOW) ? sign : 0;
+}
+
 // Shared-memory carve-up of adi_band_kernel (bytes), for tcap >= T and
 // bitmap width wmax words per lane.
 struct BandSmem {
@@ -660,6 +674,7 @@ struct BandSmem {
 //      positions and its count of BELOW frames in the reference set;
 //   5. every lane sweeps its chunk of queries: toggle the frames entering /
 //      leaving the set, walk a pointer to the t-th set bit, t = k - below.
+template <int WCAP>
 __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArgs a, int tcap, int wmin) {
   extern __shared__ __align__(16) unsigned char bsm_raw[];
   const int T = a.T;
@@ -785,13 +800,18 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
     __syncwarp();
     // ---- 3. sort the band; codes of band frames = sorted positions -------
     if (!fail) {
-      switch (W) {
-        case 1: band_sort<1>(bk, bidx, code, nb, lane); break;
-        case 2: band_sort<2>(bk, bidx, code, nb, lane); break;
-        case 4: band_sort<4>(bk, bidx, code, nb, lane); break;
-        case 8: band_sort<8>(bk, bidx, code, nb, lane); break;
-        case 16: band_sort<16>(bk, bidx, code, nb, lane); break;
-        default: band_sort<32>(bk, bidx, code, nb, lane); break;
+      // only the widths this instantiation serves are compiled in (the
+      // 32-word sort needs far more registers than the others)
+      if constexpr (WCAP <= 16) {
+        switch (W) {
+          case 1: band_sort<1>(bk, bidx, code, nb, lane); break;
+          case 2: band_sort<2>(bk, bidx, code, nb, lane); break;
+          case 4: band_sort<4>(bk, bidx, code, nb, lane); break;
+          case 8: band_sort<8>(bk, bidx, code, nb, lane); break;
+          default: band_sort<16>(bk, bidx, code, nb, lane); break;
+        }
+      } else {
+        band_sort<32>(bk, bidx, code, nb, lane);
       }
     }
   }
@@ -881,26 +901,14 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
       if (i + 3 < i1) v2 = src[(long long)perm_s[i + 3] * NN];
       const uint32_t gi = gate_at(i);
       const int Ln = (int)(gi & 0xffffu), Rn = (int)(gi >> 16);
-      for (int s = Lc; s < Ln; s++) {            // entering
-        const uint16_t cd = code[s];
-        if (cd < CODE_ABOVE) {
-          const int wq = cd >> 5;
-          bm[wq * 32 + c] ^= 1u << (cd & 31);
-          base += (wq < wi) ? 1 : 0;
-        } else {
-          cb += (cd == CODE_BELOW) ? 1 : 0;
-        }
-      }
-      for (int s = Rc; s < Rn; s++) {            // leaving
-        const uint16_t cd = code[s];
-        if (cd < CODE_ABOVE) {
-          const int wq = cd >> 5;
-          bm[wq * 32 + c] ^= 1u << (cd & 31);
-          base -= (wq < wi) ? 1 : 0;
-        } else {
-          cb -= (cd == CODE_BELOW) ? 1 : 0;
-        }
-      }
+      // frames [Lc, Ln) enter, [Rc, Rn) leave: the first two of each run
+      // without branches (the usual case is one or two), any others in a loop
+      band_toggle(code, bm, c, Lc, Lc < Ln, 1, wi, base, cb);
+      band_toggle(code, bm, c, Lc + 1, Lc + 1 < Ln, 1, wi, base, cb);
+      for (int s = Lc + 2; s < Ln; s++) band_toggle(code, bm, c, s, true, 1, wi, base, cb);
+      band_toggle(code, bm, c, Rc, Rc < Rn, -1, wi, base, cb);
+      band_toggle(code, bm, c, Rc + 1, Rc + 1 < Rn, -1, wi, base, cb);
+      for (int s = Rc + 2; s < Rn; s++) band_toggle(code, bm, c, s, true, -1, wi, base, cb);
       Lc = Ln;
       Rc = Rn;
       const int nset = Lc + (T - Rc);
@@ -978,16 +986,21 @@ cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st) {
   if (e != cudaSuccess || a.wmax == 0) return e;
   // band launches: groups whose widest bitmap is <= 16 words, then wider ones,
   // each with shared memory sized for its widest class
-  const int split = a.wmax < 16 ? a.wmax : 16;
-  const int ranges[2][2] = {{0, split}, {split, a.wmax}};
-  for (int r = 0; r < 2; r++) {
-    if (ranges[r][1] <= ranges[r][0] && r == 1) break;
+  {
     AdiArgs b = a;
-    b.wmax = ranges[r][1];
+    b.wmax = a.wmax < 16 ? a.wmax : 16;
     const BandSmem L(tcap, b.wmax);
-    e = cudaFuncSetAttribute(adi_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    e = cudaFuncSetAttribute(adi_band_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
-    adi_band_kernel<<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(b, tcap, ranges[r][0]);
+    adi_band_kernel<16><<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(b, tcap, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.wmax > 16) {
+    const BandSmem L(tcap, a.wmax);
+    e = cudaFuncSetAttribute(adi_band_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    adi_band_kernel<32><<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(a, tcap, 16);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
