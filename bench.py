@@ -377,13 +377,76 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# uneven batches: 48 cubes, sides 64..1024, 16..400 frames, shift + rotation
+# ---------------------------------------------------------------------------
+
+def run_uneven(args, rank, world, local_rank):
+    import torch
+    from paper_1510_04331_gb300 import graphic, synth
+
+    torch.cuda.set_device(local_rank)
+    spec = synth.uneven_spec(seed=3 + rank)
+    gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    cubes = [torch.randn((T, n, n), generator=gen, device="cuda") for (n, T, _, _, _) in spec]
+    outs = [torch.empty_like(c) for c in cubes]
+    dx = [sp[2] for sp in spec]
+    dy = [sp[3] for sp in spec]
+    th = [sp[4] for sp in spec]
+    frames = sum(sp[1] for sp in spec)
+    ctx = graphic.Context(local_rank)
+    tuned = None
+    if not args.no_tune:
+        sched, t_pc, t_ps = ctx.graphic_autotune(cubes, dx, dy, th, outs=outs)
+        tuned = {"schedule": sched, "best_per_cube_ms": t_pc, "best_persistent_ms": t_ps}
+    res = {}
+    for mode, name in ((graphic.BATCH_PER_CUBE, "per_cube"), (graphic.BATCH_PERSISTENT, "persistent")):
+        for _ in range(args.warmup):
+            ctx.graphic_batch_geom(cubes, dx, dy, th, outs=outs, mode=mode)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.graphic_batch_geom(cubes, dx, dy, th, outs=outs, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = {"ms_p50": statistics.median(ms), "frames_per_s": frames / (statistics.median(ms) / 1e3)}
+    # algorithmic flops of the batch (nominal 5 m log2 m per complex line transform, both ways)
+    flops = 0.0
+    for (n, T, _, _, _) in spec:
+        flops += T * sum(fft_flops_per_frame(k, n) for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2",
+                                                              "rot_pass3"))
+    ps = res["persistent"]["ms_p50"] / 1e3
+    line = {
+        "metric": "frames/s, uneven batch (shift + 3-shear rotation)", "value": res["persistent"]["frames_per_s"],
+        "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["persistent"]["ms_p50"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "48 cubes, sides from {64,128,256,512,1024}, 16-400 frames each (seeded), shifts "
+                               "U(-2,2) px, rotations U(0,360) deg", "frames": frames,
+                   "sides": [sp[0] for sp in spec], "counts": [sp[1] for sp in spec]},
+        "modes": res, "speedup_persistent_vs_per_cube": res["per_cube"]["ms_p50"] / res["persistent"]["ms_p50"],
+        "autotune": tuned,
+        "roofline": {"bound": "alu", "achieved": flops / ps / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / ps / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "batch_persistent",
+                     "algorithmic_per_launch": flops},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven"])
+    ap.add_argument("--no-tune", action="store_true", help="uneven workload: skip the autotuner")
     ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -398,6 +461,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "uneven":
+        return run_uneven(args, rank, world, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -166,6 +166,55 @@ int graphic_reduce_host(graphic_ctx *ctx, const float *host_in, int64_t n_frames
 int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_t n, const double *theta_deg,
                            void *stream);
 
+/* ---- uneven batches --------------------------------------------------------- */
+
+/* One cube of a batch: device cubes in/out (n_frames x n x n, out may equal
+ * in), host per-frame shifts (NULL: 0) and rotation angles (degrees). */
+typedef struct {
+  const float *in;
+  float *out;
+  int64_t n_frames;
+  int32_t n;
+  int32_t reserved;
+  const double *dx;
+  const double *dy;
+  const double *theta_deg;
+} graphic_batch_item;
+
+#define GRAPHIC_BATCH_PER_CUBE 0     /* the per-call passes, cube after cube          */
+#define GRAPHIC_BATCH_PERSISTENT 1   /* every frame in one persistent launch (graph)  */
+
+/*
+ * Recentre then rotate every frame of every cube of an uneven batch (cubes of
+ * different n and frame counts): out = rotate(shift(in, dx, dy), theta), the
+ * arithmetic of graphic_shift followed by graphic_rotate (Sect. 3.3.1, 3.4).
+ * GRAPHIC_BATCH_PERSISTENT runs all frames in ONE persistent kernel launch
+ * replayed from a CUDA graph while the batch keeps its layout; its work items
+ * (one group of line pairs of one pass of one frame) wait only on the
+ * previous pass of their own frame, with bounded waits
+ * (GRAPHIC_ERR_TIMEOUT).  Scratch: two waves of frames of at most the
+ * schedule's wave budget each.
+ */
+int graphic_batch_geom(graphic_ctx *ctx, const graphic_batch_item *items, int32_t n_items, int32_t mode);
+
+/*
+ * Autotuner: time the schedule candidates on this batch and keep the fastest
+ * in the context -- for the per-call passes the intermediate per chunk of
+ * frames (16..128 MiB, L2 staging) and the kernel of 1024-point lines (one
+ * warp per line pair with radix-32 stages, or the generic radix-16 kernel);
+ * for the persistent executor the wave budget and CTAs per SM.  Writes them
+ * to cache_path (JSON, may be NULL), which graphic_create reads back from the
+ * file named by the environment variable GRAPHIC_TUNE_CACHE.  best_ms (may be
+ * NULL) receives the best per-cube and persistent times (2 doubles).
+ */
+int graphic_autotune(graphic_ctx *ctx, const graphic_batch_item *items, int32_t n_items, const char *cache_path,
+                     double *best_ms);
+
+/* Schedule values, in order: chunk_mb, variant_1024, batch_budget_mb,
+ * batch_ctas_per_sm (first n of them). */
+int graphic_get_schedule(graphic_ctx *ctx, int32_t *values, int32_t n);
+int graphic_set_schedule(graphic_ctx *ctx, const int32_t *values, int32_t n);
+
 /* ---- measurement support ------------------------------------------------ */
 
 /* Kernel identifiers for graphic_profile_read. */
@@ -176,7 +225,8 @@ int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_
 #define GRAPHIC_K_ROT_P2 4
 #define GRAPHIC_K_ROT_P3 5
 #define GRAPHIC_K_COLLAPSE 6
-#define GRAPHIC_K_COUNT 7
+#define GRAPHIC_K_BATCH 7
+#define GRAPHIC_K_COUNT 8
 
 /* enable != 0: bracket every kernel launch of the context with CUDA events
  * on its stream and accumulate per-kernel device time and launch counts;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -51,6 +52,17 @@ struct graphic_ctx {
   std::vector<cudaEvent_t> ev;      // event pool, pairs
   std::vector<int> ev_kernel;       // kernel id per used pair
   size_t ev_used = 0;
+  // schedule (defaults, autotuner, or GRAPHIC_TUNE_CACHE)
+  int chunk_mb = 64;                // frames per chunk of the per-call passes: this much intermediate
+  int variant_1024 = 1;             // 1024-point lines: 1 warp per line pair (radix 32x32), 0 generic
+  int batch_budget_mb = 1024;       // persistent executor: scratch of one wave (two waves alternate)
+  int batch_ctas_per_sm = 2;
+  // persistent executor state
+  int *d_counters = nullptr;
+  size_t counters_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<long long> graph_key;
 };
 
 namespace {
@@ -178,20 +190,20 @@ int end_call(graphic_ctx *c) {
   prof_collect(c);
   if (*c->h_status & STATUS_NONFINITE) return fail(GRAPHIC_ERR_NONFINITE, "non-finite value in the input cube");
   if (*c->h_status & STATUS_INTERNAL) return fail(GRAPHIC_ERR_INTERNAL, "device consistency check failed");
+  if (*c->h_status & STATUS_TIMEOUT) return fail(GRAPHIC_ERR_TIMEOUT, "a bounded device wait ran out");
   return GRAPHIC_OK;
 }
 
-long long chunk_frames(int n, long long T, size_t bytes_per_frame) {
-  size_t budget = (size_t)64 << 20;
+long long chunk_frames(const graphic_ctx *c, long long T, size_t bytes_per_frame) {
+  size_t budget = (size_t)c->chunk_mb << 20;
   if (const char *e = getenv("GRAPHIC_CHUNK_MB")) {
     long v = atol(e);
     if (v > 0) budget = (size_t)v << 20;
   }
-  long long c = (long long)(budget / bytes_per_frame);
-  if (c < 1) c = 1;
-  if (c > T) c = T;
-  (void)n;
-  return c;
+  long long k = (long long)(budget / bytes_per_frame);
+  if (k < 1) k = 1;
+  if (k > T) k = T;
+  return k;
 }
 
 // --- shift ------------------------------------------------------------------
@@ -209,7 +221,7 @@ int validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
 int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *p_dx,
                   const double *p_dy) {
   const long long NN = (long long)n * n;
-  const long long ch = chunk_frames(n, T, (size_t)NN * sizeof(float));
+  const long long ch = chunk_frames(c, T, (size_t)NN * sizeof(float));
   for (long long f0 = 0; f0 < T; f0 += ch) {
     const long long nf = std::min<long long>(ch, T - f0);
     LineArgs a{};
@@ -222,12 +234,12 @@ int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_
     a.out_fstride = NN;
     a.n = n;
     prof_begin(c, GRAPHIC_K_SHIFT_X);
-    cudaError_t e = launch_line_pass(SHIFT_X, a, nf, c->stream);
+    cudaError_t e = launch_line_pass(SHIFT_X, a, nf, c->stream, c->variant_1024);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift x pass");
     a.in = out + f0 * NN;
     prof_begin(c, GRAPHIC_K_SHIFT_Y);
-    e = launch_line_pass(SHIFT_Y, a, nf, c->stream);
+    e = launch_line_pass(SHIFT_Y, a, nf, c->stream, c->variant_1024);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift y pass");
   }
@@ -266,7 +278,7 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
                    const double *p_s, const int *p_q) {
   const long long NN = (long long)n * n;
   const long long NM = NN * 2;
-  const long long ch = chunk_frames(n, T, (size_t)NM * sizeof(float));
+  const long long ch = chunk_frames(c, T, (size_t)NM * sizeof(float));
   int rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, (size_t)ch * NM * sizeof(float), false);
   if (rc) return rc;
   for (long long f0 = 0; f0 < T; f0 += ch) {
@@ -283,7 +295,7 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.in_fstride = NN;
     a.out_fstride = NM;
     prof_begin(c, GRAPHIC_K_ROT_P1);
-    cudaError_t e = launch_line_pass(ROT_P1, a, nf, c->stream);
+    cudaError_t e = launch_line_pass(ROT_P1, a, nf, c->stream, c->variant_1024);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 1");
     // pass 2: scratch columns, in place
@@ -292,14 +304,14 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.in_fstride = NM;
     a.out_fstride = NM;
     prof_begin(c, GRAPHIC_K_ROT_P2);
-    e = launch_line_pass(ROT_P2, a, nf, c->stream);
+    e = launch_line_pass(ROT_P2, a, nf, c->stream, c->variant_1024);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 2");
     // pass 3: scratch rows -> frame rows
     a.out = out + f0 * NN;
     a.out_fstride = NN;
     prof_begin(c, GRAPHIC_K_ROT_P3);
-    e = launch_line_pass(ROT_P3, a, nf, c->stream);
+    e = launch_line_pass(ROT_P3, a, nf, c->stream, c->variant_1024);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 3");
   }
@@ -501,6 +513,269 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   return GRAPHIC_OK;
 }
 
+// --- uneven batches -----------------------------------------------------------
+int validate_batch(const graphic_batch_item *items, int32_t n_items) {
+  if (n_items < 0 || (n_items > 0 && !items)) return fail(GRAPHIC_ERR_INVALID_ARG, "bad item list");
+  for (int32_t i = 0; i < n_items; i++) {
+    const graphic_batch_item &it = items[i];
+    int rc = check_cube(it.in, it.out, it.n_frames, it.n);
+    if (rc) return rc;
+    if (it.n_frames > 0 && !it.theta_deg) return fail(GRAPHIC_ERR_INVALID_ARG, "null theta");
+    for (int64_t t = 0; t < it.n_frames; t++) {
+      const double dx = it.dx ? it.dx[t] : 0.0, dy = it.dy ? it.dy[t] : 0.0;
+      if (!isfinite(dx) || !isfinite(dy) || fabs(dx) > it.n / 2 || fabs(dy) > it.n / 2)
+        return fail(GRAPHIC_ERR_INVALID_ARG, "shift not finite or |shift| > n/2");
+    }
+  }
+  return GRAPHIC_OK;
+}
+
+// work items (CTAs) of one frame per pass: shift x, shift y, rotation 1, 2, 3
+void batch_ctas(int n, int out[5]) {
+  const int per = n * n / 4096;   // n lines, 4096/m line pairs per CTA
+  out[0] = out[1] = out[2] = out[4] = per;
+  out[3] = 2 * per;               // 2n columns
+}
+
+// One cube after the other: the per-call shift and rotation passes, no
+// synchronisation in between.
+int batch_per_cube(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items) {
+  PlanBuilder pb;
+  std::vector<size_t> off(n_items * 5);
+  for (int32_t i = 0; i < n_items; i++) {
+    const graphic_batch_item &it = items[i];
+    const int64_t T = it.n_frames;
+    std::vector<double> dx(T, 0.0), dy(T, 0.0);
+    for (int64_t t = 0; t < T; t++) {
+      if (it.dx) dx[t] = it.dx[t];
+      if (it.dy) dy[t] = it.dy[t];
+    }
+    RotPlanHost rp;
+    int rc = plan_rotate(it.theta_deg, T, false, rp);
+    if (rc) return rc;
+    off[5 * i + 0] = pb.add(dx.data(), T * sizeof(double));
+    off[5 * i + 1] = pb.add(dy.data(), T * sizeof(double));
+    off[5 * i + 2] = pb.add(rp.a.data(), T * sizeof(double));
+    off[5 * i + 3] = pb.add(rp.s.data(), T * sizeof(double));
+    off[5 * i + 4] = pb.add(rp.q.data(), T * sizeof(int));
+  }
+  int rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  for (int32_t i = 0; i < n_items; i++) {
+    const graphic_batch_item &it = items[i];
+    if (it.n_frames == 0) continue;
+    if ((rc = enqueue_shift(c, it.in, it.out, it.n_frames, it.n, at<double>(c, off[5 * i]),
+                            at<double>(c, off[5 * i + 1]))))
+      return rc;
+    if ((rc = enqueue_rotate(c, it.out, it.out, it.n_frames, it.n, at<double>(c, off[5 * i + 2]),
+                             at<double>(c, off[5 * i + 3]), at<int>(c, off[5 * i + 4]))))
+      return rc;
+  }
+  return GRAPHIC_OK;
+}
+
+// Every frame of every cube in one persistent launch, replayed from a CUDA
+// graph while the batch keeps its layout.
+int batch_persistent(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items) {
+  std::vector<BatchFrame> fr;
+  for (int32_t i = 0; i < n_items; i++) {
+    const graphic_batch_item &it = items[i];
+    RotPlanHost rp;
+    int rc = plan_rotate(it.theta_deg, it.n_frames, false, rp);
+    if (rc) return rc;
+    const size_t NN = (size_t)it.n * it.n;
+    for (int64_t t = 0; t < it.n_frames; t++) {
+      BatchFrame b{};
+      b.in = it.in + t * NN;
+      b.out = it.out + t * NN;
+      b.dx = it.dx ? it.dx[t] : 0.0;
+      b.dy = it.dy ? it.dy[t] : 0.0;
+      b.a = rp.a[t];
+      b.s = rp.s[t];
+      b.q = rp.q[t];
+      b.n = it.n;
+      batch_ctas(it.n, b.ctas);
+      fr.push_back(b);
+    }
+  }
+  const int nframes = (int)fr.size();
+  if (nframes == 0) return GRAPHIC_OK;
+  // waves: consecutive frames whose n x 2n scratch fits the wave budget
+  const size_t budget = std::max<size_t>((size_t)c->batch_budget_mb << 20, (size_t)1024 * 2048 * 4);
+  std::vector<size_t> wave_off(nframes);
+  int waves = 0;
+  size_t used = 0, wave_max = 0;
+  for (int f = 0; f < nframes; f++) {
+    const size_t need = (size_t)fr[f].n * 2 * fr[f].n * sizeof(float);
+    if (f == 0 || used + need > budget) {
+      if (f) waves++;
+      used = 0;
+    }
+    fr[f].wave = waves;
+    wave_off[f] = used;
+    used += need;
+    wave_max = std::max(wave_max, used);
+  }
+  waves++;
+  int rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, 2 * wave_max, false);
+  if (rc) return rc;
+  for (int f = 0; f < nframes; f++)
+    fr[f].scratch = c->d_scratch + ((fr[f].wave & 1) ? wave_max / sizeof(float) : 0) + wave_off[f] / sizeof(float);
+  // segments in hand-out order
+  std::vector<BatchSeg> segs;
+  std::vector<int> wave_r3(waves, 0);
+  long long total = 0;
+  int f0 = 0;
+  for (int w = 0; w < waves; w++) {
+    int f1 = f0;
+    while (f1 < nframes && fr[f1].wave == w) f1++;
+    for (int pass = 0; pass < 5; pass++)
+      for (int f = f0; f < f1; f++) {
+        segs.push_back(BatchSeg{(int)total, f, pass, fr[f].ctas[pass]});
+        total += fr[f].ctas[pass];
+        if (pass == 4) wave_r3[w] += fr[f].ctas[pass];
+      }
+    f0 = f1;
+  }
+  if (total >= (1ll << 31)) return fail(GRAPHIC_ERR_UNSUPPORTED, "batch too large for one launch");
+  std::vector<int> seg_of_item((size_t)total);
+  for (size_t k = 0; k < segs.size(); k++)
+    for (int i = 0; i < segs[k].count; i++) seg_of_item[(size_t)segs[k].item0 + i] = (int)k;
+  PlanBuilder pb;
+  const size_t o_fr = pb.add(fr.data(), fr.size() * sizeof(BatchFrame));
+  const size_t o_sg = pb.add(segs.data(), segs.size() * sizeof(BatchSeg));
+  const size_t o_w = pb.add(wave_r3.data(), wave_r3.size() * sizeof(int));
+  const size_t o_si = pb.add(seg_of_item.data(), seg_of_item.size() * sizeof(int));
+  const size_t cbytes = sizeof(int) * (1 + 5 * (size_t)nframes + waves);
+  if ((rc = ensure((void **)&c->d_counters, &c->counters_bytes, cbytes, false))) return rc;
+  // the pinned / device plan buffers must not move under a recorded graph
+  const size_t pbytes = std::max<size_t>(pb.buf.size(), 16);
+  if ((rc = ensure((void **)&c->h_plan, &c->h_plan_bytes, pbytes, true))) return rc;
+  if ((rc = ensure((void **)&c->d_plan, &c->d_plan_bytes, pbytes, false))) return rc;
+  memcpy(c->h_plan, pb.buf.data(), pb.buf.size());
+  BatchArgs b{};
+  b.frames = reinterpret_cast<const BatchFrame *>(c->d_plan + o_fr);
+  b.segs = reinterpret_cast<const BatchSeg *>(c->d_plan + o_sg);
+  b.wave_r3 = reinterpret_cast<const int *>(c->d_plan + o_w);
+  b.seg_of_item = reinterpret_cast<const int *>(c->d_plan + o_si);
+  b.nseg = (int)segs.size();
+  b.total = (int)total;
+  b.nframes = nframes;
+  b.next = c->d_counters;
+  b.done = c->d_counters + 1;
+  b.wave_done = c->d_counters + 1 + 5 * (size_t)nframes;
+  b.status = c->d_status;
+  b.spin_limit = 2000000000ll;   // about one second of clock cycles per wait
+  const std::vector<long long> key = {(long long)(uintptr_t)c->h_plan, (long long)(uintptr_t)c->d_plan,
+                                      (long long)pb.buf.size(), (long long)o_sg, (long long)o_w, (long long)o_si,
+                                      (long long)(uintptr_t)c->d_counters, (long long)cbytes, b.nseg, b.total,
+                                      nframes, (long long)(uintptr_t)c->d_status, c->batch_ctas_per_sm,
+                                      (long long)(uintptr_t)c->stream};
+  if (c->graph_exec && key != c->graph_key) {
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+  }
+  if (!c->graph_exec) {
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_plan, c->h_plan, pb.buf.size(), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, cbytes, cs);
+    if (e == cudaSuccess) e = launch_batch_persistent(b, c->batch_ctas_per_sm, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e != cudaSuccess ? e : e2, "batch graph capture");
+    }
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->graph = g;
+    c->graph_key = key;
+  }
+  prof_begin(c, GRAPHIC_K_BATCH);
+  cudaError_t e = cudaGraphLaunch(c->graph_exec, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return GRAPHIC_OK;
+}
+
+int run_batch(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode) {
+  int rc = validate_batch(items, n_items);
+  if (rc) return rc;
+  if (mode != GRAPHIC_BATCH_PER_CUBE && mode != GRAPHIC_BATCH_PERSISTENT)
+    return fail(GRAPHIC_ERR_INVALID_ARG, "unknown batch mode");
+  if ((rc = begin_call(c))) return rc;
+  rc = (mode == GRAPHIC_BATCH_PER_CUBE) ? batch_per_cube(c, items, n_items) : batch_persistent(c, items, n_items);
+  if (rc) {
+    cudaStreamSynchronize(c->stream);
+    c->ev_used = 0;
+    return rc;
+  }
+  return end_call(c);
+}
+
+// --- schedule cache ---------------------------------------------------------
+const char *kTuneKeys[] = {"chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm"};
+
+void load_schedule(graphic_ctx *c, const char *path) {
+  if (!path || !*path) return;
+  FILE *fp = fopen(path, "r");
+  if (!fp) return;
+  char buf[4096];
+  const size_t nread = fread(buf, 1, sizeof(buf) - 1, fp);
+  fclose(fp);
+  buf[nread] = 0;
+  int *dst[] = {&c->chunk_mb, &c->variant_1024, &c->batch_budget_mb, &c->batch_ctas_per_sm};
+  for (int k = 0; k < 4; k++) {
+    char pat[64];
+    snprintf(pat, sizeof(pat), "\"%s\":", kTuneKeys[k]);
+    const char *q = strstr(buf, pat);
+    int v;
+    if (q && sscanf(q + strlen(pat), " %d", &v) == 1 && v >= 0) *dst[k] = v;
+  }
+}
+
+int save_schedule(const graphic_ctx *c, const char *path) {
+  if (!path || !*path) return GRAPHIC_OK;
+  FILE *fp = fopen(path, "w");
+  if (!fp) return fail(GRAPHIC_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  fprintf(fp, "{\"chunk_mb\": %d, \"variant_1024\": %d, \"batch_budget_mb\": %d, \"batch_ctas_per_sm\": %d}\n",
+          c->chunk_mb, c->variant_1024, c->batch_budget_mb, c->batch_ctas_per_sm);
+  fclose(fp);
+  return GRAPHIC_OK;
+}
+
+// Device milliseconds of one batch call (after one untimed call).
+int time_batch(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode, int reps, float *ms) {
+  int rc = run_batch(c, items, n_items, mode);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int r = 0; r < reps; r++) {
+    cudaEventRecord(e0, c->stream);
+    rc = run_batch(c, items, n_items, mode);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    if (rc) break;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    best = std::min(best, t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = best;
+  return rc;
+}
+
 }  // namespace
 
 int graphic::set_last_error(int code, const char *msg) { return fail(code, msg); }
@@ -536,6 +811,7 @@ int graphic_create(graphic_ctx **out, int device) {
     graphic_destroy(c);
     return cuda_fail(e, "context allocation");
   }
+  load_schedule(c, getenv("GRAPHIC_TUNE_CACHE"));
   *out = c;
   return GRAPHIC_OK;
 }
@@ -549,6 +825,14 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_scratch);
   cudaFree(c->d_cube);
   cudaFree(c->d_img);
+  cudaFree(c->d_counters);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_key.clear();
+  c->d_counters = nullptr;
+  c->counters_bytes = 0;
   c->d_plan = nullptr;
   c->h_plan = nullptr;
   c->d_scratch = nullptr;
@@ -681,6 +965,76 @@ int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t
   return end_call(c);
 }
 
+int graphic_batch_geom(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  DeviceGuard g(c->device);
+  return run_batch(c, items, n_items, mode);
+}
+
+int graphic_autotune(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, const char *cache_path,
+                     double *best_ms) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  DeviceGuard g(c->device);
+  int rc = validate_batch(items, n_items);
+  if (rc) return rc;
+  float ms;
+  // per-cube schedule: intermediate per chunk, kernel of 1024-point lines
+  int best_chunk = c->chunk_mb, best_var = c->variant_1024;
+  float best_pc = 1e30f;
+  for (int var = 0; var <= 1; var++)
+    for (int mb : {16, 32, 64, 128}) {
+      c->chunk_mb = mb;
+      c->variant_1024 = var;
+      if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_PER_CUBE, 2, &ms))) return rc;
+      if (ms < best_pc) {
+        best_pc = ms;
+        best_chunk = mb;
+        best_var = var;
+      }
+    }
+  c->chunk_mb = best_chunk;
+  c->variant_1024 = best_var;
+  // persistent executor: wave budget, CTAs per SM
+  int best_budget = c->batch_budget_mb, best_cps = c->batch_ctas_per_sm;
+  float best_ps = 1e30f;
+  for (int cps = 1; cps <= 2; cps++)
+    for (int mb : {32, 64, 128, 512, 4096}) {
+      c->batch_budget_mb = mb;
+      c->batch_ctas_per_sm = cps;
+      if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_PERSISTENT, 2, &ms))) return rc;
+      if (ms < best_ps) {
+        best_ps = ms;
+        best_budget = mb;
+        best_cps = cps;
+      }
+    }
+  c->batch_budget_mb = best_budget;
+  c->batch_ctas_per_sm = best_cps;
+  if (best_ms) {
+    best_ms[0] = best_pc;
+    best_ms[1] = best_ps;
+  }
+  return save_schedule(c, cache_path);
+}
+
+int graphic_get_schedule(graphic_ctx *c, int32_t *values, int32_t n) {
+  if (!c || !values || n < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  const int v[4] = {c->chunk_mb, c->variant_1024, c->batch_budget_mb, c->batch_ctas_per_sm};
+  for (int32_t k = 0; k < n && k < 4; k++) values[k] = v[k];
+  return GRAPHIC_OK;
+}
+
+int graphic_set_schedule(graphic_ctx *c, const int32_t *values, int32_t n) {
+  if (!c || !values || n < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  int *dst[4] = {&c->chunk_mb, &c->variant_1024, &c->batch_budget_mb, &c->batch_ctas_per_sm};
+  for (int32_t k = 0; k < n && k < 4; k++) {
+    if (values[k] < 0 || (k == 1 && values[k] > 1) || (k != 1 && values[k] == 0))
+      return fail(GRAPHIC_ERR_INVALID_ARG, "bad schedule value");
+  }
+  for (int32_t k = 0; k < n && k < 4; k++) *dst[k] = values[k];
+  return GRAPHIC_OK;
+}
+
 int graphic_profile(graphic_ctx *c, int enable) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
   c->prof = enable != 0;
@@ -705,7 +1059,7 @@ int graphic_profile_read(graphic_ctx *c, double *ms, int64_t *launches, int32_t 
 
 const char *graphic_kernel_name(int32_t k) {
   static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_median", "rot_pass1",
-                                              "rot_pass2", "rot_pass3", "collapse_median"};
+                                              "rot_pass2", "rot_pass3", "collapse_median", "batch_persistent"};
   return (k >= 0 && k < GRAPHIC_K_COUNT) ? names[k] : nullptr;
 }
 

@@ -296,37 +296,53 @@ __device__ __forceinline__ double line_shift(const LineArgs &a, long long f, int
 
 __device__ __forceinline__ bool finite_pair(float2 v) { return isfinite(v.x) && isfinite(v.y); }
 
+// Global loads of frame data: through L1 normally; L2 only (.cg) in the
+// persistent batch kernel, whose CTAs read data other CTAs of the same
+// launch wrote (L1 is not coherent across SMs).
+template <bool CG>
+__device__ __forceinline__ float ldf(const float *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+template <bool CG>
+__device__ __forceinline__ float2 ldf2(const float *p) {
+  if constexpr (CG) return __ldcg(reinterpret_cast<const float2 *>(p));
+  else return *reinterpret_cast<const float2 *>(p);
+}
+
 // Load element `pos` (< n) of row `line` of rot90^q(frame) and of row line+1.
+template <bool CG = false>
 __device__ __forceinline__ float2 load_rot90_pair(const float *__restrict__ fr, int n, int q, int line, int pos) {
   float x0 = 0.f, x1 = 0.f;
   switch (q) {
     case 0:
-      x0 = fr[(size_t)line * n + pos];
-      x1 = fr[(size_t)(line + 1) * n + pos];
+      x0 = ldf<CG>(fr + (size_t)line * n + pos);
+      x1 = ldf<CG>(fr + (size_t)(line + 1) * n + pos);
       break;
     case 1:   // g[i][j] = in[n - j][i]  (j >= 1)
       if (pos >= 1) {
-        float2 t = *reinterpret_cast<const float2 *>(fr + (size_t)(n - pos) * n + line);
+        float2 t = ldf2<CG>(fr + (size_t)(n - pos) * n + line);
         x0 = t.x;
         x1 = t.y;
       }
       break;
     case 2:   // g[i][j] = in[n - i][n - j]  (i, j >= 1)
       if (pos >= 1) {
-        if (line >= 1) x0 = fr[(size_t)(n - line) * n + (n - pos)];
-        x1 = fr[(size_t)(n - line - 1) * n + (n - pos)];
+        if (line >= 1) x0 = ldf<CG>(fr + (size_t)(n - line) * n + (n - pos));
+        x1 = ldf<CG>(fr + (size_t)(n - line - 1) * n + (n - pos));
       }
       break;
     default:  // g[i][j] = in[j][n - i]  (i >= 1)
-      if (line >= 1) x0 = fr[(size_t)pos * n + (n - line)];
-      x1 = fr[(size_t)pos * n + (n - line - 1)];
+      if (line >= 1) x0 = ldf<CG>(fr + (size_t)pos * n + (n - line));
+      x1 = ldf<CG>(fr + (size_t)pos * n + (n - line - 1));
       break;
   }
   return make_float2(x0, x1);
 }
 
-template <int M, int KIND>
-__global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
+template <int M, int KIND, bool CG = false>
+__device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, int cx, float2 *smem, LineParam *lp,
+                                               int *ident_p) {
   constexpr int N = M / 2;
   constexpr int TPL = M / 16;          // threads per line pair
   constexpr int LPC = 4096 / M;        // line pairs per CTA
@@ -336,15 +352,11 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
   constexpr int NOUT = (KIND == ROT_P1) ? M : N;       // output samples per line
   constexpr int NLINES = (KIND == ROT_P2) ? M : N;     // lines per frame
 
-  extern __shared__ float2 smem[];
-  __shared__ LineParam lp[2 * LPC];
-  __shared__ int ident_s;
-
+  int &ident_s = *ident_p;
   const int tid = threadIdx.x;
   const int p = tid / TPL;
   const int j = tid % TPL;
-  const long long f = blockIdx.y;
-  const int line0 = 2 * (blockIdx.x * LPC + p);
+  const int line0 = 2 * (cx * LPC + p);
   const float *__restrict__ fin = a.in + f * a.in_fstride;
   float *__restrict__ fout = a.out + f * a.out_fstride;
   const float2 *__restrict__ tw = d_twiddle + tw_off(M);
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
     ident_s = id ? 1 : 0;
   }
   if (tid < 2 * LPC && (!SAME_D || tid == 0)) {
-    const int gl = 2 * blockIdx.x * LPC + tid;
+    const int gl = 2 * cx * LPC + tid;
     make_param(lp[tid], line_shift<KIND>(a, f, gl, N), M);
   }
   __syncthreads();
@@ -374,11 +386,11 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
       if (pos < NIN) {
         if constexpr (KIND == SHIFT_X || KIND == ROT_P3) {
           const int rs = (KIND == ROT_P3) ? M : N;
-          z = make_float2(fin[(size_t)line0 * rs + pos], fin[(size_t)(line0 + 1) * rs + pos]);
+          z = make_float2(ldf<CG>(fin + (size_t)line0 * rs + pos), ldf<CG>(fin + (size_t)(line0 + 1) * rs + pos));
         } else if constexpr (KIND == SHIFT_Y) {
-          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+          z = ldf2<CG>(fin + (size_t)pos * N + line0);
         } else if constexpr (KIND == ROT_P1) {
-          z = load_rot90_pair(fin, N, q, line0, pos);
+          z = load_rot90_pair<CG>(fin, N, q, line0, pos);
         }
       }
       if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
@@ -403,15 +415,15 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
       float2 z = make_float2(0.f, 0.f);
       if (m * (M / 16) < NIN) {   // compile-time pruning of the zero half
         if constexpr (KIND == SHIFT_X) {
-          z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
+          z = make_float2(ldf<CG>(fin + (size_t)line0 * N + pos), ldf<CG>(fin + (size_t)(line0 + 1) * N + pos));
         } else if constexpr (KIND == SHIFT_Y) {
-          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+          z = ldf2<CG>(fin + (size_t)pos * N + line0);
         } else if constexpr (KIND == ROT_P1) {
-          z = load_rot90_pair(fin, N, q, line0, pos);
+          z = load_rot90_pair<CG>(fin, N, q, line0, pos);
         } else if constexpr (KIND == ROT_P2) {
-          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
+          z = ldf2<CG>(fin + (size_t)pos * M + line0);
         } else {
-          z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+          z = make_float2(ldf<CG>(fin + (size_t)line0 * M + pos), ldf<CG>(fin + (size_t)(line0 + 1) * M + pos));
         }
         if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
       }
@@ -499,6 +511,15 @@ __global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
     }
   }
   (void)NLINES;
+}
+
+// One CTA of a line pass: line pairs cx * LPC .. of frame blockIdx.y.
+template <int M, int KIND>
+__global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
+  extern __shared__ float2 smem[];
+  __shared__ LineParam lp[2 * (4096 / M)];
+  __shared__ int ident_s;
+  line_pass_body<M, KIND>(a, blockIdx.y, blockIdx.x, smem, lp, &ident_s);
 }
 
 // ---------------------------------------------------------------------------
@@ -770,6 +791,119 @@ cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent executor for uneven batches: frames of any supported size, each
+// shifted then rotated, in ONE launch.  Work items (one CTA-sized group of
+// line pairs of one pass of one frame) are handed out in order from an
+// atomic counter: waves of frames one after the other, within a wave pass
+// by pass (shift x, shift y, rotation passes 1-3), within a pass frame by
+// frame.  An item of pass p waits until its frame's pass p-1 items are done;
+// rotation pass 1 of wave w also waits until wave w-2 has finished (their
+// scratch slots alternate).  Every wait is on items handed out earlier, held
+// by running CTAs, so none can wait forever; the waits are still bounded
+// (clock-based), setting STATUS_TIMEOUT and moving on if a limit is hit.
+// ---------------------------------------------------------------------------
+
+template <int KIND>
+__device__ __forceinline__ void batch_pass(const BatchFrame &fr, int cx, int *status, float2 *smem, LineParam *lp,
+                                           int *ident) {
+  LineArgs la{};
+  la.status = status;
+  la.in_fstride = 0;
+  la.out_fstride = 0;
+  la.n = fr.n;
+  if constexpr (KIND == SHIFT_X) {
+    la.in = fr.in; la.out = fr.out; la.p0 = &fr.dx; la.p1 = &fr.dy;
+  } else if constexpr (KIND == SHIFT_Y) {
+    la.in = fr.out; la.out = fr.out; la.p0 = &fr.dx; la.p1 = &fr.dy;
+  } else {
+    la.p0 = &fr.a; la.p1 = &fr.s; la.q = &fr.q;
+    if constexpr (KIND == ROT_P1) { la.in = fr.out; la.out = fr.scratch; }
+    else if constexpr (KIND == ROT_P2) { la.in = fr.scratch; la.out = fr.scratch; }
+    else { la.in = fr.scratch; la.out = fr.out; }
+  }
+  // L1-bypassing loads where this SM may hold a stale line: the rotation
+  // passes read data that CTAs on other SMs wrote after this SM may have
+  // cached it (frame columns after the column shift, recycled scratch).  The
+  // shift passes read only the input (or lines only their own CTA wrote).
+  constexpr bool CG = (KIND == ROT_P1 || KIND == ROT_P2 || KIND == ROT_P3);
+  switch (fr.n) {
+    case 64: line_pass_body<128, KIND, CG>(la, 0, cx, smem, lp, ident); break;
+    case 128: line_pass_body<256, KIND, CG>(la, 0, cx, smem, lp, ident); break;
+    case 256: line_pass_body<512, KIND, CG>(la, 0, cx, smem, lp, ident); break;
+    case 512: line_pass_body<1024, KIND, CG>(la, 0, cx, smem, lp, ident); break;
+    default: line_pass_body<2048, KIND, CG>(la, 0, cx, smem, lp, ident); break;
+  }
+}
+
+// Wait until *ctr >= target.  Gives up after `limit` clock cycles, or at once
+// when an earlier wait of the launch already gave up (so a launch with a
+// broken dependency ends after one limit, not one limit per item).
+__device__ __forceinline__ bool wait_at_least(const int *ctr, int target, long long limit, const int *status) {
+  const long long t0 = clock64();
+  while (*(volatile const int *)ctr < target) {
+    if ((*(volatile const int *)status & STATUS_TIMEOUT) || clock64() - t0 > limit) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Items are taken BATCH_GRAB at a time with one atomic; the next grab is
+// issued before the current group is processed, hiding its latency.
+constexpr int BATCH_GRAB = 4;
+
+__global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchArgs b) {
+  extern __shared__ float2 smem[];
+  __shared__ LineParam lp[2 * 32];
+  __shared__ int ident_s;
+  __shared__ int grab_s[2];
+  __shared__ int seg_s;
+  const int tid = threadIdx.x;
+  if (tid == 0) grab_s[0] = atomicAdd(b.next, BATCH_GRAB);
+  int slot = 0;
+  for (;;) {
+    __syncthreads();
+    const int g0 = grab_s[slot];
+    if (g0 >= b.total) break;
+    if (tid == 0) grab_s[slot ^ 1] = atomicAdd(b.next, BATCH_GRAB);   // next group, in flight
+    const int g1 = min(g0 + BATCH_GRAB, b.total);
+    for (int it = g0; it < g1; it++) {
+      if (tid == 0) {
+        const int sgi = __ldg(&b.seg_of_item[it]);
+        seg_s = sgi;
+        const BatchSeg sg = b.segs[sgi];
+        bool ok = true;
+        if (sg.pass > 0) ok = wait_at_least(&b.done[(sg.pass - 1) * b.nframes + sg.frame],
+                                            b.frames[sg.frame].ctas[sg.pass - 1], b.spin_limit, b.status);
+        if (ok && sg.pass == 2) {
+          const int w = b.frames[sg.frame].wave;
+          if (w >= 2) ok = wait_at_least(&b.wave_done[w - 2], b.wave_r3[w - 2], b.spin_limit, b.status);
+        }
+        if (!ok) atomicOr(b.status, STATUS_TIMEOUT);
+        __threadfence();
+      }
+      __syncthreads();
+      const BatchSeg sg = b.segs[seg_s];
+      const BatchFrame &fr = b.frames[sg.frame];
+      const int cx = it - sg.item0;
+      switch (sg.pass) {
+        case 0: batch_pass<SHIFT_X>(fr, cx, b.status, smem, lp, &ident_s); break;
+        case 1: batch_pass<SHIFT_Y>(fr, cx, b.status, smem, lp, &ident_s); break;
+        case 2: batch_pass<ROT_P1>(fr, cx, b.status, smem, lp, &ident_s); break;
+        case 3: batch_pass<ROT_P2>(fr, cx, b.status, smem, lp, &ident_s); break;
+        default: batch_pass<ROT_P3>(fr, cx, b.status, smem, lp, &ident_s); break;
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        atomicAdd(&b.done[sg.pass * b.nframes + sg.frame], 1);
+        if (sg.pass == 4) atomicAdd(&b.wave_done[fr.wave], 1);
+      }
+    }
+    slot ^= 1;
+  }
+}
+
 template <int M>
 size_t line_smem_bytes() {
   constexpr int LPC = 4096 / M;
@@ -821,6 +955,11 @@ cudaError_t launch_m(LineKind kind, const LineArgs &a, long long n_frames, cudaS
 }  // namespace
 
 int geom_init_device() {
+  // the persistent batch kernel is launched inside stream capture: set its
+  // shared-memory limit here, per device, outside any capture
+  if (cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)line_smem_bytes<1024>()) != cudaSuccess)
+    return -1;
   static float2 host[kTwTotal];
   static bool filled = false;
   if (!filled) {
@@ -834,13 +973,26 @@ int geom_init_device() {
   return cudaMemcpyToSymbol(d_twiddle, host, sizeof(host)) == cudaSuccess ? 0 : -1;
 }
 
-cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st) {
+cudaError_t launch_batch_persistent(const BatchArgs &b, int ctas_per_sm, cudaStream_t st) {
+  const size_t smem = line_smem_bytes<1024>();   // the same for every line length
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long grid = (long long)sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+  if (grid > b.total) grid = b.total;
+  if (grid < 1) return cudaSuccess;
+  batch_persistent_kernel<<<(unsigned)grid, 256, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st, int variant_1024) {
   if (n_frames <= 0) return cudaSuccess;
   switch (a.n) {
     case 64: return launch_m<128>(kind, a, n_frames, st);
     case 128: return launch_m<256>(kind, a, n_frames, st);
     case 256: return launch_m<512>(kind, a, n_frames, st);
     case 512:
+      if (!variant_1024) return launch_m<1024>(kind, a, n_frames, st);
       switch (kind) {
         case SHIFT_X: return launch_w32<SHIFT_X>(a, n_frames, st);
         case SHIFT_Y: return launch_w32<SHIFT_Y>(a, n_frames, st);

@@ -34,10 +34,48 @@ int set_last_error(int code, const char *msg);
 // Device status bits.
 constexpr int STATUS_NONFINITE = 1;
 constexpr int STATUS_INTERNAL = 2;
+constexpr int STATUS_TIMEOUT = 4;
 
 // geom.cu
 int geom_init_device();   // uploads the twiddle tables of the current device (0 = ok)
-cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st);
+// variant_1024: 1024-point lines by one warp per line pair (1) or the generic kernel (0)
+cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st,
+                             int variant_1024 = 1);
+
+// Uneven batches (one persistent launch): per-frame descriptor ...
+struct BatchFrame {
+  const float *in;       // n x n input frame
+  float *out;            // n x n output frame (shift then rotation)
+  float *scratch;        // n x 2n scratch slot of this frame's wave
+  double dx, dy;         // recentring shift
+  double a, s;           // tan(theta'/2), sin(theta')
+  int q;                 // quarter turns
+  int n;                 // frame side
+  int wave;              // wave index (scratch ring slot = wave & 1)
+  int ctas[5];           // work items of passes shift x, shift y, rotation 1, 2, 3
+};
+// ... and the work segments in hand-out order.
+struct BatchSeg {
+  int item0;             // first item of the segment
+  int frame;
+  int pass;              // 0..4
+  int count;
+};
+struct BatchArgs {
+  const BatchFrame *frames;
+  const BatchSeg *segs;
+  const int *seg_of_item;  // [total] segment of each item
+  int nseg;
+  int total;             // items in all
+  int nframes;
+  int *next;             // hand-out counter (zeroed before the launch)
+  int *done;             // [5][nframes] finished items per (pass, frame) (zeroed)
+  int *wave_done;        // [waves] finished rotation-pass-3 items per wave (zeroed)
+  const int *wave_r3;    // [waves] rotation-pass-3 items per wave
+  int *status;
+  long long spin_limit;  // clock cycles a wait may take before STATUS_TIMEOUT
+};
+cudaError_t launch_batch_persistent(const BatchArgs &b, int ctas_per_sm, cudaStream_t st);
 
 // median.cu
 struct AdiArgs {

@@ -30,7 +30,19 @@ ERRORS = {
     -6: "GRAPHIC_ERR_TIMEOUT",
     -7: "GRAPHIC_ERR_INTERNAL",
 }
-KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median"]
+KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median",
+           "batch_persistent"]
+BATCH_PER_CUBE = 0
+BATCH_PERSISTENT = 1
+SCHEDULE_KEYS = ["chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm"]
+
+
+class BatchItem(ctypes.Structure):
+    """graphic_batch_item of include/graphic.h."""
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dx", ctypes.POINTER(ctypes.c_double)), ("dy", ctypes.POINTER(ctypes.c_double)),
+                ("theta_deg", ctypes.POINTER(ctypes.c_double))]
 MAX_FRAMES_MEDIAN = 2048
 
 
@@ -66,6 +78,10 @@ _SIGS = {
     "graphic_kernel_name": [_I32],
     "graphic_rotate_noalloc": [_P, _P, _I64, _I32, _D, _P],
     "graphic_workspace_bytes": [_P, ctypes.POINTER(_I64)],
+    "graphic_batch_geom": [_P, _P, _I32, _I32],
+    "graphic_autotune": [_P, _P, _I32, ctypes.c_char_p, _D],
+    "graphic_get_schedule": [_P, ctypes.POINTER(_I32), _I32],
+    "graphic_set_schedule": [_P, ctypes.POINTER(_I32), _I32],
 }
 
 
@@ -212,6 +228,51 @@ class Context:
         _check(lib().graphic_reduce_host(self.h, _P(ptr), T, n, pdx, pdy, ppa, float(fwhm), float(n_fwhm),
                                          ea.ctypes.data_as(_D), ea.size, _P(optr)))
         return out_host
+
+    def _batch(self, cubes, outs, dx, dy, theta):
+        keep = []
+        arr = (BatchItem * len(cubes))()
+        for i, (c, o) in enumerate(zip(cubes, outs)):
+            c = _cube(c)
+            o = _cube(o, "out")
+            T, n = c.shape[0], c.shape[1]
+            a = [_f64(v, T) for v in (dx[i], dy[i], theta[i])]
+            keep.append(a)
+            arr[i] = BatchItem(c.data_ptr(), o.data_ptr(), T, n, 0, a[0][1], a[1][1], a[2][1])
+        return arr, keep
+
+    def graphic_batch_geom(self, cubes, dx, dy, theta, outs=None, mode=BATCH_PERSISTENT):
+        """Shift then rotate every frame of every cube (cubes of different n
+        and frame counts); mode BATCH_PERSISTENT: one persistent launch."""
+        import torch
+        outs = [torch.empty_like(c) for c in cubes] if outs is None else outs
+        arr, keep = self._batch(cubes, outs, dx, dy, theta)
+        self._stream()
+        _check(lib().graphic_batch_geom(self.h, ctypes.cast(arr, _P), len(cubes), int(mode)))
+        return outs
+
+    def graphic_autotune(self, cubes, dx, dy, theta, outs=None, cache_path=None):
+        """Time the schedule candidates on this batch; returns (schedule dict,
+        best per-cube ms, best persistent ms)."""
+        import torch
+        outs = [torch.empty_like(c) for c in cubes] if outs is None else outs
+        arr, keep = self._batch(cubes, outs, dx, dy, theta)
+        best = (ctypes.c_double * 2)()
+        self._stream()
+        _check(lib().graphic_autotune(self.h, ctypes.cast(arr, _P), len(cubes),
+                                      cache_path.encode() if cache_path else None, best))
+        return self.schedule(), best[0], best[1]
+
+    def schedule(self):
+        v = (_I32 * 4)()
+        _check(lib().graphic_get_schedule(self.h, v, 4))
+        return dict(zip(SCHEDULE_KEYS, list(v)))
+
+    def set_schedule(self, **kw):
+        cur = self.schedule()
+        cur.update(kw)
+        v = (_I32 * 4)(*[int(cur[k]) for k in SCHEDULE_KEYS])
+        _check(lib().graphic_set_schedule(self.h, v, 4))
 
     def profile(self, enable: bool):
         _check(lib().graphic_profile(self.h, int(bool(enable))))

@@ -199,3 +199,33 @@ def random_frames(T: int, N: int, seed: int, smooth: bool = False, dtype=np.floa
             sx, sy = rng.uniform(3.0, smax), rng.uniform(3.0, smax)
             out[t] += (rng.uniform(0.5, 2.0) * np.exp(-((xx - x0) ** 2 / (2 * sx * sx) + (yy - y0) ** 2 / (2 * sy * sy)))).astype(dtype)
     return out
+
+
+def uneven_spec(seed: int = 3, n_cubes: int = 48, sides=(64, 128, 256, 512, 1024), t_range=(16, 400),
+                max_shift: float = 2.0):
+    """Shapes and per-frame parameters of an uneven batch: sides drawn from
+    ``sides``, frame counts uniform in ``t_range``, shifts U(-2, 2) px,
+    rotations U(0, 360) deg.  Returns a list of (n, T, dx, dy, theta)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_cubes):
+        n = int(rng.choice(sides))
+        T = int(rng.integers(t_range[0], t_range[1] + 1))
+        out.append((n, T, rng.uniform(-max_shift, max_shift, T), rng.uniform(-max_shift, max_shift, T),
+                    rng.uniform(0.0, 360.0, T)))
+    return out
+
+
+def uneven_batch(seed: int = 3, n_cubes: int = 48, sides=(64, 128, 256, 512, 1024), t_range=(16, 400),
+                 max_shift: float = 2.0):
+    """An uneven batch with its frames: white noise plus a Gaussian star at
+    the centre (content does not matter to the geometry, the sizes do).
+    Returns a list of (cube float32 [T][n][n], dx, dy, theta)."""
+    rng = np.random.default_rng(seed + 7919)
+    out = []
+    for (n, T, dx, dy, th) in uneven_spec(seed, n_cubes, sides, t_range, max_shift):
+        cube = rng.standard_normal((T, n, n), dtype=np.float32)
+        yy, xx = np.mgrid[0:n, 0:n]
+        cube += (100.0 * np.exp(-((xx - n / 2) ** 2 + (yy - n / 2) ** 2) / (2 * 1.7 ** 2))).astype(np.float32)
+        out.append((cube, dx, dy, th))
+    return out
