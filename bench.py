@@ -397,10 +397,12 @@ def run_uneven(args, rank, world, local_rank):
     ctx = graphic.Context(local_rank)
     tuned = None
     if not args.no_tune:
-        sched, t_pc, t_ps = ctx.graphic_autotune(cubes, dx, dy, th, outs=outs)
-        tuned = {"schedule": sched, "best_per_cube_ms": t_pc, "best_persistent_ms": t_ps}
+        sched, t_pc, t_ps, t_gr = ctx.graphic_autotune(cubes, dx, dy, th, outs=outs)
+        tuned = {"schedule": sched, "best_per_cube_ms": t_pc, "best_persistent_ms": t_ps, "best_grouped_ms": t_gr}
     res = {}
-    for mode, name in ((graphic.BATCH_PER_CUBE, "per_cube"), (graphic.BATCH_PERSISTENT, "persistent")):
+    modes = ((graphic.BATCH_PER_CUBE, "per_cube"), (graphic.BATCH_PERSISTENT, "persistent"),
+             (graphic.BATCH_GROUPED, "grouped"))
+    for mode, name in modes:
         for _ in range(args.warmup):
             ctx.graphic_batch_geom(cubes, dx, dy, th, outs=outs, mode=mode)
         torch.cuda.synchronize()
@@ -414,24 +416,27 @@ def run_uneven(args, rank, world, local_rank):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         res[name] = {"ms_p50": statistics.median(ms), "frames_per_s": frames / (statistics.median(ms) / 1e3)}
+    batched = "grouped" if ctx.schedule()["batch_mode"] == graphic.BATCH_GROUPED else "persistent"
     # algorithmic flops of the batch (nominal 5 m log2 m per complex line transform, both ways)
     flops = 0.0
     for (n, T, _, _, _) in spec:
         flops += T * sum(fft_flops_per_frame(k, n) for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2",
                                                               "rot_pass3"))
-    ps = res["persistent"]["ms_p50"] / 1e3
+    bs = res[batched]["ms_p50"] / 1e3
     line = {
-        "metric": "frames/s, uneven batch (shift + 3-shear rotation)", "value": res["persistent"]["frames_per_s"],
+        "metric": "frames/s, uneven batch (shift + 3-shear rotation)", "value": res[batched]["frames_per_s"],
         "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["persistent"]["ms_p50"], "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": res[batched]["ms_p50"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "48 cubes, sides from {64,128,256,512,1024}, 16-400 frames each (seeded), shifts "
                                "U(-2,2) px, rotations U(0,360) deg", "frames": frames,
-                   "sides": [sp[0] for sp in spec], "counts": [sp[1] for sp in spec]},
-        "modes": res, "speedup_persistent_vs_per_cube": res["per_cube"]["ms_p50"] / res["persistent"]["ms_p50"],
+                   "sides": [sp[0] for sp in spec], "counts": [sp[1] for sp in spec],
+                   "l2": "inputs larger than L2 (%.1f GB)" % (sum(c.numel() for c in cubes) * 4 / 1e9)},
+        "batched_mode": batched, "modes": res,
+        "speedup_batched_vs_per_cube": res["per_cube"]["ms_p50"] / res[batched]["ms_p50"],
         "autotune": tuned,
-        "roofline": {"bound": "alu", "achieved": flops / ps / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / ps / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "batch_persistent",
+        "roofline": {"bound": "alu", "achieved": flops / bs / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / bs / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "batch_" + batched,
                      "algorithmic_per_launch": flops},
     }
     if rank == 0:

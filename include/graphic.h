@@ -169,49 +169,68 @@ int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_
 /* ---- uneven batches --------------------------------------------------------- */
 
 /* One cube of a batch: device cubes in/out (n_frames x n x n, out may equal
- * in), host per-frame shifts (NULL: 0) and rotation angles (degrees). */
+ * in), host per-frame shifts (NULL: 0) and rotation angles (degrees; may be
+ * NULL when the item does not rotate), and which steps to apply. */
 typedef struct {
   const float *in;
   float *out;
   int64_t n_frames;
   int32_t n;
-  int32_t reserved;
+  int32_t passes;              /* GRAPHIC_PASS_* mask; 0 means both steps */
   const double *dx;
   const double *dy;
   const double *theta_deg;
 } graphic_batch_item;
 
+#define GRAPHIC_PASS_SHIFT 1         /* recentring shift (Sect. 3.3.1)                */
+#define GRAPHIC_PASS_ROTATE 2        /* three-shear rotation (Sect. 3.4)              */
+
 #define GRAPHIC_BATCH_PER_CUBE 0     /* the per-call passes, cube after cube          */
 #define GRAPHIC_BATCH_PERSISTENT 1   /* every frame in one persistent launch (graph)  */
+#define GRAPHIC_BATCH_GROUPED 2      /* per-size launches over frame tables (graph)   */
+#define GRAPHIC_BATCH_AUTO 3         /* the mode the schedule names (autotuner)       */
 
 /*
- * Recentre then rotate every frame of every cube of an uneven batch (cubes of
- * different n and frame counts): out = rotate(shift(in, dx, dy), theta), the
- * arithmetic of graphic_shift followed by graphic_rotate (Sect. 3.3.1, 3.4).
- * GRAPHIC_BATCH_PERSISTENT runs all frames in ONE persistent kernel launch
- * replayed from a CUDA graph while the batch keeps its layout; its work items
- * (one group of line pairs of one pass of one frame) wait only on the
- * previous pass of their own frame, with bounded waits
- * (GRAPHIC_ERR_TIMEOUT).  Scratch: two waves of frames of at most the
- * schedule's wave budget each.
+ * Recentre and/or rotate every frame of every cube of an uneven batch (cubes
+ * of different n and frame counts): out = rotate(shift(in, dx, dy), theta)
+ * with both steps, the arithmetic of graphic_shift followed by
+ * graphic_rotate (Sect. 3.3.1, 3.4); one step when `passes` names one.
+ *   GRAPHIC_BATCH_PERSISTENT  all frames in ONE persistent kernel launch
+ *     replayed from a CUDA graph while the batch keeps its layout; its work
+ *     items (one group of line pairs of one pass of one frame) wait only on
+ *     the previous pass of their own frame, with bounded waits
+ *     (GRAPHIC_ERR_TIMEOUT).  Scratch: two waves of at most the schedule's
+ *     batch_budget_mb each.
+ *   GRAPHIC_BATCH_GROUPED  frames sorted by size into waves whose scratch
+ *     fits group_budget_mb (L2-sized); each pass of a wave is one launch of
+ *     that size's kernel over a table of frame pointers; waves run on
+ *     group_streams concurrent branches of one CUDA graph (wave w reuses the
+ *     scratch of wave w - group_streams), replayed while the layout holds.
+ * Items may not overlap one another, except that an item's out may equal its
+ * own in.  Synchronous: returns after the device finished.
  */
 int graphic_batch_geom(graphic_ctx *ctx, const graphic_batch_item *items, int32_t n_items, int32_t mode);
 
 /*
  * Autotuner: time the schedule candidates on this batch and keep the fastest
  * in the context -- for the per-call passes the intermediate per chunk of
- * frames (16..128 MiB, L2 staging) and the kernel of 1024-point lines (one
+ * frames (16..256 MiB, L2 staging) and the kernel of 1024-point lines (one
  * warp per line pair with radix-32 stages, or the generic radix-16 kernel);
- * for the persistent executor the wave budget and CTAs per SM.  Writes them
- * to cache_path (JSON, may be NULL), which graphic_create reads back from the
- * file named by the environment variable GRAPHIC_TUNE_CACHE.  best_ms (may be
- * NULL) receives the best per-cube and persistent times (2 doubles).
+ * for the persistent executor the wave budget and CTAs per SM; for the
+ * grouped executor the wave budget and the number of concurrent branches;
+ * then the fastest batched mode (batch_mode, used by GRAPHIC_BATCH_AUTO).
+ * Writes them to cache_path (JSON, may be NULL), which graphic_create reads
+ * back from the file named by the environment variable GRAPHIC_TUNE_CACHE.
+ * best_ms (may be NULL) receives the best per-cube, persistent and grouped
+ * times (3 doubles).
  */
 int graphic_autotune(graphic_ctx *ctx, const graphic_batch_item *items, int32_t n_items, const char *cache_path,
                      double *best_ms);
 
 /* Schedule values, in order: chunk_mb, variant_1024, batch_budget_mb,
- * batch_ctas_per_sm (first n of them). */
+ * batch_ctas_per_sm, group_budget_mb, group_streams (1..8), batch_mode
+ * (GRAPHIC_BATCH_PERSISTENT or GRAPHIC_BATCH_GROUPED) -- the first n. */
+#define GRAPHIC_SCHEDULE_LEN 7
 int graphic_get_schedule(graphic_ctx *ctx, int32_t *values, int32_t n);
 int graphic_set_schedule(graphic_ctx *ctx, const int32_t *values, int32_t n);
 

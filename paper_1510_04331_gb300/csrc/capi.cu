@@ -57,6 +57,17 @@ struct graphic_ctx {
   int variant_1024 = 1;             // 1024-point lines: 1 warp per line pair (radix 32x32), 0 generic
   int batch_budget_mb = 1024;       // persistent executor: scratch of one wave (two waves alternate)
   int batch_ctas_per_sm = 2;
+  int group_budget_mb = 128;        // grouped executor: scratch of one wave
+  int group_streams = 2;            // grouped executor: concurrent graph branches
+  int batch_mode = GRAPHIC_BATCH_GROUPED;   // GRAPHIC_BATCH_AUTO resolves to this
+  // grouped executor state
+  float *d_gscratch = nullptr;
+  size_t gscratch_bytes = 0;
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gevents;
+  cudaGraph_t ggraph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<long long> gkey;
   // persistent executor state
   int *d_counters = nullptr;
   size_t counters_bytes = 0;
@@ -514,13 +525,20 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
 }
 
 // --- uneven batches -----------------------------------------------------------
+int item_passes(const graphic_batch_item &it) {
+  return it.passes ? it.passes : (GRAPHIC_PASS_SHIFT | GRAPHIC_PASS_ROTATE);
+}
+
 int validate_batch(const graphic_batch_item *items, int32_t n_items) {
   if (n_items < 0 || (n_items > 0 && !items)) return fail(GRAPHIC_ERR_INVALID_ARG, "bad item list");
   for (int32_t i = 0; i < n_items; i++) {
     const graphic_batch_item &it = items[i];
     int rc = check_cube(it.in, it.out, it.n_frames, it.n);
     if (rc) return rc;
-    if (it.n_frames > 0 && !it.theta_deg) return fail(GRAPHIC_ERR_INVALID_ARG, "null theta");
+    if (it.passes < 0 || it.passes > (GRAPHIC_PASS_SHIFT | GRAPHIC_PASS_ROTATE))
+      return fail(GRAPHIC_ERR_INVALID_ARG, "bad passes mask");
+    if (it.n_frames > 0 && (item_passes(it) & GRAPHIC_PASS_ROTATE) && !it.theta_deg)
+      return fail(GRAPHIC_ERR_INVALID_ARG, "null theta");
     for (int64_t t = 0; t < it.n_frames; t++) {
       const double dx = it.dx ? it.dx[t] : 0.0, dy = it.dy ? it.dy[t] : 0.0;
       if (!isfinite(dx) || !isfinite(dy) || fabs(dx) > it.n / 2 || fabs(dy) > it.n / 2)
@@ -551,8 +569,14 @@ int batch_per_cube(graphic_ctx *c, const graphic_batch_item *items, int32_t n_it
       if (it.dy) dy[t] = it.dy[t];
     }
     RotPlanHost rp;
-    int rc = plan_rotate(it.theta_deg, T, false, rp);
-    if (rc) return rc;
+    if (item_passes(it) & GRAPHIC_PASS_ROTATE) {
+      int rc = plan_rotate(it.theta_deg, T, false, rp);
+      if (rc) return rc;
+    } else {
+      rp.a.assign(T, 0.0);
+      rp.s.assign(T, 0.0);
+      rp.q.assign(T, 0);
+    }
     off[5 * i + 0] = pb.add(dx.data(), T * sizeof(double));
     off[5 * i + 1] = pb.add(dy.data(), T * sizeof(double));
     off[5 * i + 2] = pb.add(rp.a.data(), T * sizeof(double));
@@ -564,10 +588,13 @@ int batch_per_cube(graphic_ctx *c, const graphic_batch_item *items, int32_t n_it
   for (int32_t i = 0; i < n_items; i++) {
     const graphic_batch_item &it = items[i];
     if (it.n_frames == 0) continue;
-    if ((rc = enqueue_shift(c, it.in, it.out, it.n_frames, it.n, at<double>(c, off[5 * i]),
-                            at<double>(c, off[5 * i + 1]))))
+    const int ps = item_passes(it);
+    if ((ps & GRAPHIC_PASS_SHIFT) && (rc = enqueue_shift(c, it.in, it.out, it.n_frames, it.n,
+                                                         at<double>(c, off[5 * i]), at<double>(c, off[5 * i + 1]))))
       return rc;
-    if ((rc = enqueue_rotate(c, it.out, it.out, it.n_frames, it.n, at<double>(c, off[5 * i + 2]),
+    const float *rin = (ps & GRAPHIC_PASS_SHIFT) ? it.out : it.in;
+    if ((ps & GRAPHIC_PASS_ROTATE) &&
+        (rc = enqueue_rotate(c, rin, it.out, it.n_frames, it.n, at<double>(c, off[5 * i + 2]),
                              at<double>(c, off[5 * i + 3]), at<int>(c, off[5 * i + 4]))))
       return rc;
   }
@@ -580,21 +607,29 @@ int batch_persistent(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   std::vector<BatchFrame> fr;
   for (int32_t i = 0; i < n_items; i++) {
     const graphic_batch_item &it = items[i];
+    const int ps = item_passes(it);
     RotPlanHost rp;
-    int rc = plan_rotate(it.theta_deg, it.n_frames, false, rp);
-    if (rc) return rc;
+    if (ps & GRAPHIC_PASS_ROTATE) {
+      int rc = plan_rotate(it.theta_deg, it.n_frames, false, rp);
+      if (rc) return rc;
+    }
     const size_t NN = (size_t)it.n * it.n;
     for (int64_t t = 0; t < it.n_frames; t++) {
       BatchFrame b{};
       b.in = it.in + t * NN;
       b.out = it.out + t * NN;
+      b.rin = (ps & GRAPHIC_PASS_SHIFT) ? b.out : b.in;
       b.dx = it.dx ? it.dx[t] : 0.0;
       b.dy = it.dy ? it.dy[t] : 0.0;
-      b.a = rp.a[t];
-      b.s = rp.s[t];
-      b.q = rp.q[t];
+      if (ps & GRAPHIC_PASS_ROTATE) {
+        b.a = rp.a[t];
+        b.s = rp.s[t];
+        b.q = rp.q[t];
+      }
       b.n = it.n;
       batch_ctas(it.n, b.ctas);
+      if (!(ps & GRAPHIC_PASS_SHIFT)) b.ctas[0] = b.ctas[1] = 0;
+      if (!(ps & GRAPHIC_PASS_ROTATE)) b.ctas[2] = b.ctas[3] = b.ctas[4] = 0;
       fr.push_back(b);
     }
   }
@@ -606,7 +641,7 @@ int batch_persistent(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   int waves = 0;
   size_t used = 0, wave_max = 0;
   for (int f = 0; f < nframes; f++) {
-    const size_t need = (size_t)fr[f].n * 2 * fr[f].n * sizeof(float);
+    const size_t need = fr[f].ctas[2] ? (size_t)fr[f].n * 2 * fr[f].n * sizeof(float) : 0;
     if (f == 0 || used + need > budget) {
       if (f) waves++;
       used = 0;
@@ -631,6 +666,7 @@ int batch_persistent(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
     while (f1 < nframes && fr[f1].wave == w) f1++;
     for (int pass = 0; pass < 5; pass++)
       for (int f = f0; f < f1; f++) {
+        if (!fr[f].ctas[pass]) continue;
         segs.push_back(BatchSeg{(int)total, f, pass, fr[f].ctas[pass]});
         total += fr[f].ctas[pass];
         if (pass == 4) wave_r3[w] += fr[f].ctas[pass];
@@ -706,13 +742,210 @@ int batch_persistent(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   return GRAPHIC_OK;
 }
 
+// Grouped executor.  Frames sorted by (size, steps) and cut into waves whose
+// rotation scratch fits group_budget_mb; a wave's passes are launches of that
+// size's line-pass kernel over frame-pointer tables.  Waves are dealt round
+// robin to group_streams branches of one captured graph: a branch runs its
+// waves in order, so wave w reuses the scratch slot of wave w - branches only
+// after it finished.  The graph is kept while the layout (wave shapes,
+// buffers, stream) is unchanged; per call only the plan is rewritten.
+struct GroupWave {
+  int n, mask, f0, nf;
+};
+
+void drop_group_graph(graphic_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->ggraph) cudaGraphDestroy(c->ggraph);
+  c->gexec = nullptr;
+  c->ggraph = nullptr;
+  c->gkey.clear();
+}
+
+int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items) {
+  struct Fr {
+    const float *in;
+    float *out;
+    double dx, dy, a, s;
+    int q, n, mask;
+  };
+  std::vector<Fr> fr;
+  for (int32_t i = 0; i < n_items; i++) {
+    const graphic_batch_item &it = items[i];
+    const int ps = item_passes(it);
+    RotPlanHost rp;
+    if (ps & GRAPHIC_PASS_ROTATE) {
+      int rc = plan_rotate(it.theta_deg, it.n_frames, false, rp);
+      if (rc) return rc;
+    }
+    const size_t NN = (size_t)it.n * it.n;
+    for (int64_t t = 0; t < it.n_frames; t++) {
+      Fr f{};
+      f.in = it.in + t * NN;
+      f.out = it.out + t * NN;
+      f.dx = it.dx ? it.dx[t] : 0.0;
+      f.dy = it.dy ? it.dy[t] : 0.0;
+      if (ps & GRAPHIC_PASS_ROTATE) {
+        f.a = rp.a[t];
+        f.s = rp.s[t];
+        f.q = rp.q[t];
+      }
+      f.n = it.n;
+      f.mask = ps;
+      fr.push_back(f);
+    }
+  }
+  const int nframes = (int)fr.size();
+  if (nframes == 0) return GRAPHIC_OK;
+  // largest frames first (their launches are the long ones), stable otherwise
+  std::stable_sort(fr.begin(), fr.end(), [](const Fr &x, const Fr &y) {
+    return x.n != y.n ? x.n > y.n : x.mask < y.mask;
+  });
+  const size_t budget = (size_t)c->group_budget_mb << 20;
+  std::vector<GroupWave> waves;
+  size_t slot_bytes = 0;
+  for (int f = 0; f < nframes;) {
+    const int n = fr[f].n, mask = fr[f].mask;
+    // the wave's bytes: rotation scratch (n x 2n), else the frames themselves
+    const size_t per = (mask & GRAPHIC_PASS_ROTATE) ? (size_t)n * 2 * n * sizeof(float) : (size_t)n * n * sizeof(float);
+    int g = f;
+    size_t used = 0;
+    while (g < nframes && fr[g].n == n && fr[g].mask == mask && (g == f || used + per <= budget)) {
+      used += per;
+      g++;
+    }
+    waves.push_back(GroupWave{n, mask, f, g - f});
+    if (mask & GRAPHIC_PASS_ROTATE) slot_bytes = std::max(slot_bytes, used);
+    f = g;
+  }
+  const int R = std::max(1, std::min<int>(c->group_streams, (int)waves.size()));
+  int rc;
+  if (slot_bytes && (rc = ensure((void **)&c->d_gscratch, &c->gscratch_bytes, slot_bytes * R, false))) return rc;
+  // plan: per frame tables in the sorted order
+  std::vector<const float *> tin(nframes), trin(nframes);
+  std::vector<float *> tout(nframes);
+  std::vector<double> pdx(nframes), pdy(nframes), pa(nframes), ps(nframes);
+  std::vector<int> pq(nframes);
+  for (int f = 0; f < nframes; f++) {
+    tin[f] = fr[f].in;
+    tout[f] = fr[f].out;
+    trin[f] = (fr[f].mask & GRAPHIC_PASS_SHIFT) ? fr[f].out : fr[f].in;
+    pdx[f] = fr[f].dx;
+    pdy[f] = fr[f].dy;
+    pa[f] = fr[f].a;
+    ps[f] = fr[f].s;
+    pq[f] = fr[f].q;
+  }
+  PlanBuilder pb;
+  const size_t o_in = pb.add(tin.data(), nframes * sizeof(void *));
+  const size_t o_out = pb.add(tout.data(), nframes * sizeof(void *));
+  const size_t o_rin = pb.add(trin.data(), nframes * sizeof(void *));
+  const size_t o_dx = pb.add(pdx.data(), nframes * sizeof(double));
+  const size_t o_dy = pb.add(pdy.data(), nframes * sizeof(double));
+  const size_t o_a = pb.add(pa.data(), nframes * sizeof(double));
+  const size_t o_s = pb.add(ps.data(), nframes * sizeof(double));
+  const size_t o_q = pb.add(pq.data(), nframes * sizeof(int));
+  const size_t pbytes = std::max<size_t>(pb.buf.size(), 16);
+  if ((rc = ensure((void **)&c->h_plan, &c->h_plan_bytes, pbytes, true))) return rc;
+  if ((rc = ensure((void **)&c->d_plan, &c->d_plan_bytes, pbytes, false))) return rc;
+  memcpy(c->h_plan, pb.buf.data(), pb.buf.size());
+  std::vector<long long> key = {(long long)(uintptr_t)c->h_plan, (long long)(uintptr_t)c->d_plan,
+                                (long long)pb.buf.size(), (long long)(uintptr_t)c->d_gscratch, (long long)slot_bytes,
+                                (long long)(uintptr_t)c->d_status, R, c->variant_1024,
+                                (long long)(uintptr_t)c->stream};
+  for (const GroupWave &w : waves) {
+    key.push_back(w.n);
+    key.push_back(w.mask);
+    key.push_back(w.nf);
+  }
+  if (c->gexec && key != c->gkey) drop_group_graph(c);
+  if (!c->gexec) {
+    while ((int)c->gstreams.size() < R) {
+      cudaStream_t st;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      c->gstreams.push_back(st);
+      cudaEvent_t ev;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      c->gevents.push_back(ev);
+    }
+    cudaStream_t s0 = c->gstreams[0];
+    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_plan, c->h_plan, pb.buf.size(), cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = cudaEventRecord(c->gevents[0], s0);
+    for (int r = 1; r < R && e == cudaSuccess; r++) e = cudaStreamWaitEvent(c->gstreams[r], c->gevents[0], 0);
+    for (size_t wi = 0; wi < waves.size() && e == cudaSuccess; wi++) {
+      const GroupWave &w = waves[wi];
+      const int r = (int)(wi % R);
+      cudaStream_t st = c->gstreams[r];
+      const long long NM = 2ll * w.n * w.n;
+      LineArgs a{};
+      a.status = c->d_status;
+      a.n = w.n;
+      if (w.mask & GRAPHIC_PASS_SHIFT) {
+        a.in_tab = at<const float *>(c, o_in) + w.f0;
+        a.out_tab = at<float *>(c, o_out) + w.f0;
+        a.p0 = at<double>(c, o_dx) + w.f0;
+        a.p1 = at<double>(c, o_dy) + w.f0;
+        e = launch_line_pass(SHIFT_X, a, w.nf, st, c->variant_1024);
+        a.in_tab = at<const float *>(c, o_out) + w.f0;
+        if (e == cudaSuccess) e = launch_line_pass(SHIFT_Y, a, w.nf, st, c->variant_1024);
+      }
+      if ((w.mask & GRAPHIC_PASS_ROTATE) && e == cudaSuccess) {
+        float *slot = c->d_gscratch + (size_t)r * (slot_bytes / sizeof(float));
+        LineArgs b{};
+        b.status = c->d_status;
+        b.n = w.n;
+        b.p0 = at<double>(c, o_a) + w.f0;
+        b.p1 = at<double>(c, o_s) + w.f0;
+        b.q = at<int>(c, o_q) + w.f0;
+        b.in_tab = at<const float *>(c, o_rin) + w.f0;
+        b.out = slot;
+        b.out_fstride = NM;
+        e = launch_line_pass(ROT_P1, b, w.nf, st, c->variant_1024);
+        b.in_tab = nullptr;
+        b.in = slot;
+        b.in_fstride = NM;
+        if (e == cudaSuccess) e = launch_line_pass(ROT_P2, b, w.nf, st, c->variant_1024);
+        b.out = nullptr;
+        b.out_tab = at<float *>(c, o_out) + w.f0;
+        if (e == cudaSuccess) e = launch_line_pass(ROT_P3, b, w.nf, st, c->variant_1024);
+      }
+    }
+    for (int r = 1; r < R && e == cudaSuccess; r++) {
+      e = cudaEventRecord(c->gevents[r], c->gstreams[r]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->gevents[r], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s0, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e != cudaSuccess ? e : e2, "grouped batch graph capture");
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      c->gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->ggraph = g;
+    c->gkey = key;
+  }
+  prof_begin(c, GRAPHIC_K_BATCH);
+  cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return GRAPHIC_OK;
+}
+
 int run_batch(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode) {
   int rc = validate_batch(items, n_items);
   if (rc) return rc;
-  if (mode != GRAPHIC_BATCH_PER_CUBE && mode != GRAPHIC_BATCH_PERSISTENT)
+  if (mode == GRAPHIC_BATCH_AUTO) mode = c->batch_mode;
+  if (mode != GRAPHIC_BATCH_PER_CUBE && mode != GRAPHIC_BATCH_PERSISTENT && mode != GRAPHIC_BATCH_GROUPED)
     return fail(GRAPHIC_ERR_INVALID_ARG, "unknown batch mode");
   if ((rc = begin_call(c))) return rc;
-  rc = (mode == GRAPHIC_BATCH_PER_CUBE) ? batch_per_cube(c, items, n_items) : batch_persistent(c, items, n_items);
+  rc = (mode == GRAPHIC_BATCH_PER_CUBE)     ? batch_per_cube(c, items, n_items)
+       : (mode == GRAPHIC_BATCH_PERSISTENT) ? batch_persistent(c, items, n_items)
+                                            : batch_grouped(c, items, n_items);
   if (rc) {
     cudaStreamSynchronize(c->stream);
     c->ev_used = 0;
@@ -722,7 +955,24 @@ int run_batch(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, 
 }
 
 // --- schedule cache ---------------------------------------------------------
-const char *kTuneKeys[] = {"chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm"};
+const char *kTuneKeys[GRAPHIC_SCHEDULE_LEN] = {"chunk_mb",        "variant_1024",  "batch_budget_mb",
+                                              "batch_ctas_per_sm", "group_budget_mb", "group_streams",
+                                              "batch_mode"};
+
+void schedule_slots(graphic_ctx *c, int *dst[GRAPHIC_SCHEDULE_LEN]) {
+  int *v[GRAPHIC_SCHEDULE_LEN] = {&c->chunk_mb,        &c->variant_1024,  &c->batch_budget_mb, &c->batch_ctas_per_sm,
+                                  &c->group_budget_mb, &c->group_streams, &c->batch_mode};
+  for (int k = 0; k < GRAPHIC_SCHEDULE_LEN; k++) dst[k] = v[k];
+}
+
+bool schedule_value_ok(int k, int v) {
+  switch (k) {
+    case 1: return v == 0 || v == 1;
+    case 5: return v >= 1 && v <= 8;
+    case 6: return v == GRAPHIC_BATCH_PERSISTENT || v == GRAPHIC_BATCH_GROUPED;
+    default: return v > 0;
+  }
+}
 
 void load_schedule(graphic_ctx *c, const char *path) {
   if (!path || !*path) return;
@@ -732,22 +982,26 @@ void load_schedule(graphic_ctx *c, const char *path) {
   const size_t nread = fread(buf, 1, sizeof(buf) - 1, fp);
   fclose(fp);
   buf[nread] = 0;
-  int *dst[] = {&c->chunk_mb, &c->variant_1024, &c->batch_budget_mb, &c->batch_ctas_per_sm};
-  for (int k = 0; k < 4; k++) {
+  int *dst[GRAPHIC_SCHEDULE_LEN];
+  schedule_slots(c, dst);
+  for (int k = 0; k < GRAPHIC_SCHEDULE_LEN; k++) {
     char pat[64];
     snprintf(pat, sizeof(pat), "\"%s\":", kTuneKeys[k]);
     const char *q = strstr(buf, pat);
     int v;
-    if (q && sscanf(q + strlen(pat), " %d", &v) == 1 && v >= 0) *dst[k] = v;
+    if (q && sscanf(q + strlen(pat), " %d", &v) == 1 && schedule_value_ok(k, v)) *dst[k] = v;
   }
 }
 
-int save_schedule(const graphic_ctx *c, const char *path) {
+int save_schedule(graphic_ctx *c, const char *path) {
   if (!path || !*path) return GRAPHIC_OK;
   FILE *fp = fopen(path, "w");
   if (!fp) return fail(GRAPHIC_ERR_INVALID_ARG, std::string("cannot write ") + path);
-  fprintf(fp, "{\"chunk_mb\": %d, \"variant_1024\": %d, \"batch_budget_mb\": %d, \"batch_ctas_per_sm\": %d}\n",
-          c->chunk_mb, c->variant_1024, c->batch_budget_mb, c->batch_ctas_per_sm);
+  int *v[GRAPHIC_SCHEDULE_LEN];
+  schedule_slots(c, v);
+  fprintf(fp, "{");
+  for (int k = 0; k < GRAPHIC_SCHEDULE_LEN; k++) fprintf(fp, "%s\"%s\": %d", k ? ", " : "", kTuneKeys[k], *v[k]);
+  fprintf(fp, "}\n");
   fclose(fp);
   return GRAPHIC_OK;
 }
@@ -826,6 +1080,10 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_cube);
   cudaFree(c->d_img);
   cudaFree(c->d_counters);
+  cudaFree(c->d_gscratch);
+  c->d_gscratch = nullptr;
+  c->gscratch_bytes = 0;
+  drop_group_graph(c);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
@@ -849,6 +1107,8 @@ int graphic_destroy(graphic_ctx *c) {
   cudaFree(c->d_status);
   cudaFreeHost(c->h_status);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->gevents) cudaEventDestroy(e);
+  for (cudaStream_t st : c->gstreams) cudaStreamDestroy(st);
   delete c;
   return GRAPHIC_OK;
 }
@@ -982,7 +1242,7 @@ int graphic_autotune(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   int best_chunk = c->chunk_mb, best_var = c->variant_1024;
   float best_pc = 1e30f;
   for (int var = 0; var <= 1; var++)
-    for (int mb : {16, 32, 64, 128}) {
+    for (int mb : {16, 32, 64, 128, 256}) {
       c->chunk_mb = mb;
       c->variant_1024 = var;
       if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_PER_CUBE, 2, &ms))) return rc;
@@ -998,7 +1258,7 @@ int graphic_autotune(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   int best_budget = c->batch_budget_mb, best_cps = c->batch_ctas_per_sm;
   float best_ps = 1e30f;
   for (int cps = 1; cps <= 2; cps++)
-    for (int mb : {32, 64, 128, 512, 4096}) {
+    for (int mb : {128, 4096}) {
       c->batch_budget_mb = mb;
       c->batch_ctas_per_sm = cps;
       if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_PERSISTENT, 2, &ms))) return rc;
@@ -1010,28 +1270,46 @@ int graphic_autotune(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
     }
   c->batch_budget_mb = best_budget;
   c->batch_ctas_per_sm = best_cps;
+  // grouped executor: wave budget, concurrent branches
+  int best_gb = c->group_budget_mb, best_gs = c->group_streams;
+  float best_gr = 1e30f;
+  for (int gs : {1, 2, 3, 4})
+    for (int mb : {32, 64, 128, 256}) {
+      c->group_budget_mb = mb;
+      c->group_streams = gs;
+      if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_GROUPED, 2, &ms))) return rc;
+      if (ms < best_gr) {
+        best_gr = ms;
+        best_gb = mb;
+        best_gs = gs;
+      }
+    }
+  c->group_budget_mb = best_gb;
+  c->group_streams = best_gs;
+  c->batch_mode = (best_gr <= best_ps) ? GRAPHIC_BATCH_GROUPED : GRAPHIC_BATCH_PERSISTENT;
   if (best_ms) {
     best_ms[0] = best_pc;
     best_ms[1] = best_ps;
+    best_ms[2] = best_gr;
   }
   return save_schedule(c, cache_path);
 }
 
 int graphic_get_schedule(graphic_ctx *c, int32_t *values, int32_t n) {
   if (!c || !values || n < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
-  const int v[4] = {c->chunk_mb, c->variant_1024, c->batch_budget_mb, c->batch_ctas_per_sm};
-  for (int32_t k = 0; k < n && k < 4; k++) values[k] = v[k];
+  int *v[GRAPHIC_SCHEDULE_LEN];
+  schedule_slots(c, v);
+  for (int32_t k = 0; k < n && k < GRAPHIC_SCHEDULE_LEN; k++) values[k] = *v[k];
   return GRAPHIC_OK;
 }
 
 int graphic_set_schedule(graphic_ctx *c, const int32_t *values, int32_t n) {
   if (!c || !values || n < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
-  int *dst[4] = {&c->chunk_mb, &c->variant_1024, &c->batch_budget_mb, &c->batch_ctas_per_sm};
-  for (int32_t k = 0; k < n && k < 4; k++) {
-    if (values[k] < 0 || (k == 1 && values[k] > 1) || (k != 1 && values[k] == 0))
-      return fail(GRAPHIC_ERR_INVALID_ARG, "bad schedule value");
-  }
-  for (int32_t k = 0; k < n && k < 4; k++) *dst[k] = values[k];
+  int *dst[GRAPHIC_SCHEDULE_LEN];
+  schedule_slots(c, dst);
+  for (int32_t k = 0; k < n && k < GRAPHIC_SCHEDULE_LEN; k++)
+    if (!schedule_value_ok(k, values[k])) return fail(GRAPHIC_ERR_INVALID_ARG, "bad schedule value");
+  for (int32_t k = 0; k < n && k < GRAPHIC_SCHEDULE_LEN; k++) *dst[k] = values[k];
   return GRAPHIC_OK;
 }
 
@@ -1065,7 +1343,8 @@ const char *graphic_kernel_name(int32_t k) {
 
 int graphic_workspace_bytes(graphic_ctx *c, int64_t *bytes) {
   if (!c || !bytes) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
-  *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->cube_bytes + c->img_bytes);
+  *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->gscratch_bytes + c->cube_bytes + c->img_bytes +
+                     c->counters_bytes);
   return GRAPHIC_OK;
 }
 

@@ -357,8 +357,8 @@ __device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, i
   const int p = tid / TPL;
   const int j = tid % TPL;
   const int line0 = 2 * (cx * LPC + p);
-  const float *__restrict__ fin = a.in + f * a.in_fstride;
-  float *__restrict__ fout = a.out + f * a.out_fstride;
+  const float *__restrict__ fin = a.in_tab ? a.in_tab[f] : a.in + f * a.in_fstride;
+  float *__restrict__ fout = a.out_tab ? a.out_tab[f] : a.out + f * a.out_fstride;
   const float2 *__restrict__ tw = d_twiddle + tw_off(M);
   float2 *bufA = smem + p * LBUF;
   float2 *bufB = smem + (LPC + p) * LBUF;
@@ -635,8 +635,8 @@ __global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
   const int lane = threadIdx.x & 31, p = threadIdx.x >> 5;
   const long long f = blockIdx.y;
   const int line0 = 2 * (blockIdx.x * PPC + p);
-  const float *__restrict__ fin = a.in + f * a.in_fstride;
-  float *__restrict__ fout = a.out + f * a.out_fstride;
+  const float *__restrict__ fin = a.in_tab ? a.in_tab[f] : a.in + f * a.in_fstride;
+  float *__restrict__ fout = a.out_tab ? a.out_tab[f] : a.out + f * a.out_fstride;
   const float2 *__restrict__ tw = d_twiddle + tw_off(M);
   float2 *buf = sbuf[p];
   const int q = (KIND == ROT_P1) ? (a.q[f] & 3) : 0;
@@ -783,6 +783,8 @@ cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
     b.p0 = a.p0 ? a.p0 + f0 : nullptr;
     b.p1 = a.p1 ? a.p1 + f0 : nullptr;
     b.q = a.q ? a.q + f0 : nullptr;
+    b.in_tab = a.in_tab ? a.in_tab + f0 : nullptr;
+    b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
     dim3 grid(NLINES / (2 * PPC), (unsigned)nf);
     line_pass_w32<KIND><<<grid, 32 * PPC, 0, st>>>(b);
     cudaError_t e = cudaGetLastError();
@@ -818,7 +820,7 @@ __device__ __forceinline__ void batch_pass(const BatchFrame &fr, int cx, int *st
     la.in = fr.out; la.out = fr.out; la.p0 = &fr.dx; la.p1 = &fr.dy;
   } else {
     la.p0 = &fr.a; la.p1 = &fr.s; la.q = &fr.q;
-    if constexpr (KIND == ROT_P1) { la.in = fr.out; la.out = fr.scratch; }
+    if constexpr (KIND == ROT_P1) { la.in = fr.rin; la.out = fr.scratch; }
     else if constexpr (KIND == ROT_P2) { la.in = fr.scratch; la.out = fr.scratch; }
     else { la.in = fr.scratch; la.out = fr.out; }
   }
@@ -916,14 +918,7 @@ cudaError_t launch_one(const LineArgs &a, long long n_frames, cudaStream_t st) {
   constexpr int N = M / 2;
   constexpr int LPC = 4096 / M;
   constexpr int NLINES = (KIND == ROT_P2) ? M : N;
-  const size_t smem = line_smem_bytes<M>();
-  static bool configured = false;   // per process; attribute is per function
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(line_pass_kernel<M, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  const size_t smem = line_smem_bytes<M>();   // limit raised by geom_init_device
   for (long long f0 = 0; f0 < n_frames; f0 += 65535) {
     const long long nf = (n_frames - f0 < 65535) ? (n_frames - f0) : 65535;
     LineArgs b = a;
@@ -932,6 +927,8 @@ cudaError_t launch_one(const LineArgs &a, long long n_frames, cudaStream_t st) {
     b.p0 = a.p0 ? a.p0 + f0 : nullptr;
     b.p1 = a.p1 ? a.p1 + f0 : nullptr;
     b.q = a.q ? a.q + f0 : nullptr;
+    b.in_tab = a.in_tab ? a.in_tab + f0 : nullptr;
+    b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
     dim3 grid(NLINES / (2 * LPC), (unsigned)nf);
     line_pass_kernel<M, KIND><<<grid, 256, smem, st>>>(b);
     cudaError_t e = cudaGetLastError();
@@ -952,9 +949,25 @@ cudaError_t launch_m(LineKind kind, const LineArgs &a, long long n_frames, cudaS
   return cudaErrorInvalidValue;
 }
 
+// Raise the dynamic shared-memory limit of every generic line-pass kernel of
+// length M (done once per device at set-up, outside any stream capture).
+template <int M>
+bool configure_m() {
+  const int smem = (int)line_smem_bytes<M>();
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  return cudaFuncSetAttribute(line_pass_kernel<M, SHIFT_X>, at, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(line_pass_kernel<M, SHIFT_Y>, at, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(line_pass_kernel<M, ROT_P1>, at, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(line_pass_kernel<M, ROT_P2>, at, smem) == cudaSuccess &&
+         cudaFuncSetAttribute(line_pass_kernel<M, ROT_P3>, at, smem) == cudaSuccess;
+}
+
 }  // namespace
 
 int geom_init_device() {
+  if (!(configure_m<128>() && configure_m<256>() && configure_m<512>() && configure_m<1024>() &&
+        configure_m<2048>()))
+    return -1;
   // the persistent batch kernel is launched inside stream capture: set its
   // shared-memory limit here, per device, outside any capture
   if (cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -25,6 +25,8 @@ struct LineArgs {
   long long in_fstride;  // elements between consecutive frames of `in`
   long long out_fstride; // elements between consecutive frames of `out`
   int n;                 // frame side
+  const float *const *in_tab;  // optional: frame f reads in_tab[f] instead of in + f in_fstride
+  float *const *out_tab;       // optional: frame f writes out_tab[f] instead of out + f out_fstride
 };
 
 // Record `msg` as the calling thread's last error (graphic_last_error) and
@@ -46,13 +48,14 @@ cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frame
 struct BatchFrame {
   const float *in;       // n x n input frame
   float *out;            // n x n output frame (shift then rotation)
+  const float *rin;      // input of the rotation: out after a shift, else in
   float *scratch;        // n x 2n scratch slot of this frame's wave
   double dx, dy;         // recentring shift
   double a, s;           // tan(theta'/2), sin(theta')
   int q;                 // quarter turns
   int n;                 // frame side
   int wave;              // wave index (scratch ring slot = wave & 1)
-  int ctas[5];           // work items of passes shift x, shift y, rotation 1, 2, 3
+  int ctas[5];           // work items of passes shift x, shift y, rotation 1, 2, 3 (0: pass not applied)
 };
 // ... and the work segments in hand-out order.
 struct BatchSeg {

@@ -34,13 +34,18 @@ KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pa
            "batch_persistent"]
 BATCH_PER_CUBE = 0
 BATCH_PERSISTENT = 1
-SCHEDULE_KEYS = ["chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm"]
+BATCH_GROUPED = 2
+BATCH_AUTO = 3
+PASS_SHIFT = 1
+PASS_ROTATE = 2
+SCHEDULE_KEYS = ["chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm", "group_budget_mb",
+                 "group_streams", "batch_mode"]
 
 
 class BatchItem(ctypes.Structure):
     """graphic_batch_item of include/graphic.h."""
     _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
-                ("n", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("dx", ctypes.POINTER(ctypes.c_double)), ("dy", ctypes.POINTER(ctypes.c_double)),
                 ("theta_deg", ctypes.POINTER(ctypes.c_double))]
 MAX_FRAMES_MEDIAN = 2048
@@ -229,50 +234,60 @@ class Context:
                                          ea.ctypes.data_as(_D), ea.size, _P(optr)))
         return out_host
 
-    def _batch(self, cubes, outs, dx, dy, theta):
+    def _batch(self, cubes, outs, dx, dy, theta, passes=None):
         keep = []
         arr = (BatchItem * len(cubes))()
         for i, (c, o) in enumerate(zip(cubes, outs)):
             c = _cube(c)
             o = _cube(o, "out")
             T, n = c.shape[0], c.shape[1]
-            a = [_f64(v, T) for v in (dx[i], dy[i], theta[i])]
+            a = [(None, None) if v is None else _f64(v, T) for v in (dx[i], dy[i], theta[i])]
             keep.append(a)
-            arr[i] = BatchItem(c.data_ptr(), o.data_ptr(), T, n, 0, a[0][1], a[1][1], a[2][1])
+            arr[i] = BatchItem(c.data_ptr(), o.data_ptr(), T, n, 0 if passes is None else int(passes[i]),
+                               a[0][1], a[1][1], a[2][1])
         return arr, keep
 
-    def graphic_batch_geom(self, cubes, dx, dy, theta, outs=None, mode=BATCH_PERSISTENT):
+    def graphic_batch_geom(self, cubes, dx, dy, theta, outs=None, mode=BATCH_AUTO, passes=None):
         """Shift then rotate every frame of every cube (cubes of different n
-        and frame counts); mode BATCH_PERSISTENT: one persistent launch."""
+        and frame counts); ``passes[i]`` (PASS_SHIFT / PASS_ROTATE mask, 0 =
+        both) limits cube i to one step, whose unused parameters may be None.
+        mode: BATCH_PER_CUBE, BATCH_PERSISTENT (one persistent launch),
+        BATCH_GROUPED (per-size launches in one graph) or BATCH_AUTO (the
+        schedule's mode)."""
         import torch
         outs = [torch.empty_like(c) for c in cubes] if outs is None else outs
-        arr, keep = self._batch(cubes, outs, dx, dy, theta)
+        arr, keep = self._batch(cubes, outs, dx, dy, theta, passes)
         self._stream()
         _check(lib().graphic_batch_geom(self.h, ctypes.cast(arr, _P), len(cubes), int(mode)))
         return outs
 
     def graphic_autotune(self, cubes, dx, dy, theta, outs=None, cache_path=None):
         """Time the schedule candidates on this batch; returns (schedule dict,
-        best per-cube ms, best persistent ms)."""
+        best per-cube ms, best persistent ms, best grouped ms)."""
         import torch
         outs = [torch.empty_like(c) for c in cubes] if outs is None else outs
         arr, keep = self._batch(cubes, outs, dx, dy, theta)
-        best = (ctypes.c_double * 2)()
+        best = (ctypes.c_double * 3)()
         self._stream()
         _check(lib().graphic_autotune(self.h, ctypes.cast(arr, _P), len(cubes),
                                       cache_path.encode() if cache_path else None, best))
-        return self.schedule(), best[0], best[1]
+        return self.schedule(), best[0], best[1], best[2]
 
     def schedule(self):
-        v = (_I32 * 4)()
-        _check(lib().graphic_get_schedule(self.h, v, 4))
+        k = len(SCHEDULE_KEYS)
+        v = (_I32 * k)()
+        _check(lib().graphic_get_schedule(self.h, v, k))
         return dict(zip(SCHEDULE_KEYS, list(v)))
 
     def set_schedule(self, **kw):
         cur = self.schedule()
+        unknown = set(kw) - set(SCHEDULE_KEYS)
+        if unknown:
+            raise ValueError(f"unknown schedule keys {sorted(unknown)}")
         cur.update(kw)
-        v = (_I32 * 4)(*[int(cur[k]) for k in SCHEDULE_KEYS])
-        _check(lib().graphic_set_schedule(self.h, v, 4))
+        k = len(SCHEDULE_KEYS)
+        v = (_I32 * k)(*[int(cur[key]) for key in SCHEDULE_KEYS])
+        _check(lib().graphic_set_schedule(self.h, v, k))
 
     def profile(self, enable: bool):
         _check(lib().graphic_profile(self.h, int(bool(enable))))

@@ -1,7 +1,8 @@
 """Uneven batches (cubes of different sizes and frame counts): the persistent
-single-launch executor and the per-cube mode both equal graphic_shift then
-graphic_rotate cube by cube (bit-identical: the same line arithmetic), and
-the autotuner's schedule round-trips through its cache file."""
+single-launch executor, the grouped executor and the per-cube mode all equal
+graphic_shift then graphic_rotate cube by cube (bit-identical: the same line
+arithmetic), one-step items (shift only, rotation only) equal the one-step
+calls, and the autotuner's schedule round-trips through its cache file."""
 import json
 import os
 
@@ -12,6 +13,8 @@ from paper_1510_04331_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+PER_CUBE, PERSISTENT, GROUPED = 0, 1, 2
 
 
 @pytest.fixture(scope="module")
@@ -25,55 +28,107 @@ def batch():
     return synth.uneven_batch(seed=3, n_cubes=14, sides=(64, 128, 256, 512, 1024), t_range=(1, 9))
 
 
-def _reference(g, batch, variant_1024=0):
-    """graphic_shift then graphic_rotate cube by cube.  variant_1024 = 0: the
-    generic radix-16 kernel for 1024-point lines, the one the persistent
-    executor runs, so that the comparison can be bit-exact."""
+def _args(batch):
+    return [b[1] for b in batch], [b[2] for b in batch], [b[3] for b in batch]
+
+
+def _reference(g, batch, variant_1024=0, passes=None):
+    """graphic_shift then graphic_rotate cube by cube (or the one step that
+    passes[i] names).  variant_1024 = 0: the generic radix-16 kernel for
+    1024-point lines, the one the persistent executor runs, so that the
+    comparison can be bit-exact."""
     ctx = g.Context(0)
     ctx.set_schedule(variant_1024=variant_1024)
     out = []
-    for cube, dx, dy, th in batch:
+    for i, (cube, dx, dy, th) in enumerate(batch):
+        ps = 3 if passes is None or passes[i] == 0 else passes[i]
         c = torch.from_numpy(cube).cuda()
-        out.append(ctx.graphic_rotate(ctx.graphic_shift(c, dx, dy), th).cpu().numpy())
+        if ps & 1:
+            c = ctx.graphic_shift(c, dx, dy)
+        if ps & 2:
+            c = ctx.graphic_rotate(c, th)
+        out.append(c.cpu().numpy())
     ctx.close()
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [PER_CUBE, PERSISTENT, GROUPED])
 def test_batch_modes_equal_per_call_passes(g, batch, mode):
     ctx = g.Context(0)
     ctx.set_schedule(variant_1024=0)
     ref = _reference(g, batch)
     cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in batch]
-    for rep in range(2):   # the second persistent call replays the recorded graph
-        outs = ctx.graphic_batch_geom(cubes, [b[1] for b in batch], [b[2] for b in batch], [b[3] for b in batch],
-                                      mode=mode)
+    for rep in range(2):   # the second call replays the recorded graph
+        outs = ctx.graphic_batch_geom(cubes, *_args(batch), mode=mode)
         for o, r in zip(outs, ref):
             assert np.array_equal(o.cpu().numpy(), r)
     ctx.close()
 
 
-def test_batch_persistent_matches_default_kernels_within_tolerance(g, batch):
+@pytest.mark.parametrize("mode", [PERSISTENT, GROUPED])
+def test_batch_matches_default_kernels_within_tolerance(g, batch, mode):
     """Against the default schedule (radix-32 warp kernel for 1024-point
-    lines): equal within 1e-5 of each cube's peak."""
+    lines): equal within 1e-5 of each cube's peak; the grouped executor runs
+    the same kernels and stays bit-exact."""
     ref = _reference(g, batch, variant_1024=1)
     cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in batch]
-    outs = g.context().graphic_batch_geom(cubes, [b[1] for b in batch], [b[2] for b in batch],
-                                          [b[3] for b in batch], mode=1)
-    for o, r, b in zip(outs, ref, batch):
-        assert np.abs(o.cpu().numpy() - r).max() <= 1e-5 * np.abs(b[0]).max()
-
-
-def test_batch_persistent_small_waves_and_in_place(g, batch):
-    """Waves far smaller than the batch (the scratch ring alternates many
-    times) and in-place cubes."""
     ctx = g.Context(0)
-    ctx.set_schedule(batch_budget_mb=9, batch_ctas_per_sm=1)
+    outs = ctx.graphic_batch_geom(cubes, *_args(batch), mode=mode)
+    for o, r, b in zip(outs, ref, batch):
+        if mode == GROUPED:
+            assert np.array_equal(o.cpu().numpy(), r)
+        else:
+            assert np.abs(o.cpu().numpy() - r).max() <= 1e-5 * np.abs(b[0]).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", [PER_CUBE, PERSISTENT, GROUPED])
+def test_batch_one_step_items(g, batch, mode):
+    """Shift-only, rotation-only and two-step items mixed in one batch (the
+    serving loop's stages); a rotation-only item's unused shifts may be None
+    and a shift-only item's angles too."""
+    passes = [(1, 2, 0)[i % 3] for i in range(len(batch))]
+    ref = _reference(g, batch, passes=passes)
+    ctx = g.Context(0)
+    ctx.set_schedule(variant_1024=0)
+    cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in batch]
+    dx, dy, th = _args(batch)
+    dx = [None if p == 2 else v for p, v in zip(passes, dx)]
+    dy = [None if p == 2 else v for p, v in zip(passes, dy)]
+    th = [None if p == 1 else v for p, v in zip(passes, th)]
+    outs = ctx.graphic_batch_geom(cubes, dx, dy, th, mode=mode, passes=passes)
+    for o, r in zip(outs, ref):
+        assert np.array_equal(o.cpu().numpy(), r)
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode,sched", [(PERSISTENT, dict(batch_budget_mb=9, batch_ctas_per_sm=1)),
+                                        (GROUPED, dict(group_budget_mb=5, group_streams=3))])
+def test_batch_small_waves_and_in_place(g, batch, mode, sched):
+    """Waves far smaller than the batch (the scratch ring cycles many times)
+    and in-place cubes."""
+    ctx = g.Context(0)
+    ctx.set_schedule(variant_1024=0, **sched)
     ref = _reference(g, batch)
     cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in batch]
-    ctx.graphic_batch_geom(cubes, [b[1] for b in batch], [b[2] for b in batch], [b[3] for b in batch],
-                           outs=cubes, mode=1)
+    ctx.graphic_batch_geom(cubes, *_args(batch), outs=cubes, mode=mode)
     for o, r in zip(cubes, ref):
+        assert np.array_equal(o.cpu().numpy(), r)
+    ctx.close()
+
+
+def test_grouped_graph_follows_new_pointers(g, batch):
+    """Same layout, other cubes: the recorded graph is replayed with the new
+    frame tables (the plan is rewritten every call)."""
+    ctx = g.Context(0)
+    ctx.set_schedule(variant_1024=0)
+    sub = batch[:5]
+    ref = _reference(g, sub)
+    a = [torch.from_numpy(c).cuda() for c, _, _, _ in sub]
+    b = [x.clone() for x in a]
+    ctx.graphic_batch_geom(a, *_args(sub), mode=GROUPED)
+    outs = ctx.graphic_batch_geom(b, *_args(sub), mode=GROUPED)
+    for o, r in zip(outs, ref):
         assert np.array_equal(o.cpu().numpy(), r)
     ctx.close()
 
@@ -81,10 +136,11 @@ def test_batch_persistent_small_waves_and_in_place(g, batch):
 def test_autotune_writes_and_reloads_schedule(g, batch, tmp_path):
     path = str(tmp_path / "tune.json")
     ctx = g.Context(0)
-    cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in batch[:6]]
-    sched, t_pc, t_ps = ctx.graphic_autotune(cubes, [b[1] for b in batch[:6]], [b[2] for b in batch[:6]],
-                                             [b[3] for b in batch[:6]], cache_path=path)
-    assert t_pc > 0 and t_ps > 0
+    sub = batch[:6]
+    cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in sub]
+    sched, t_pc, t_ps, t_gr = ctx.graphic_autotune(cubes, *_args(sub), cache_path=path)
+    assert t_pc > 0 and t_ps > 0 and t_gr > 0
+    assert sched["batch_mode"] == (GROUPED if t_gr <= t_ps else PERSISTENT)
     assert json.load(open(path)) == sched
     ctx.close()
     os.environ["GRAPHIC_TUNE_CACHE"] = path
@@ -94,3 +150,15 @@ def test_autotune_writes_and_reloads_schedule(g, batch, tmp_path):
         ctx2.close()
     finally:
         del os.environ["GRAPHIC_TUNE_CACHE"]
+
+
+def test_batch_rejects_bad_passes_and_modes(g, batch):
+    ctx = g.Context(0)
+    cubes = [torch.from_numpy(batch[0][0]).cuda()]
+    with pytest.raises(g.GraphicError):
+        ctx.graphic_batch_geom(cubes, *_args(batch[:1]), passes=[4])
+    with pytest.raises(g.GraphicError):
+        ctx.graphic_batch_geom(cubes, *_args(batch[:1]), mode=7)
+    with pytest.raises(g.GraphicError):
+        ctx.set_schedule(group_streams=9)
+    ctx.close()
