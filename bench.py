@@ -368,6 +368,10 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_serve and world == 1:
+        del cube, work
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(local_rank, n_req=args.serve_requests, max_active=args.serve_max_active)
     if not args.no_cpu_baseline and world == 1:
         cb = cpu_baseline(d, budget_s=args.ref_budget)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -375,6 +379,134 @@ def run_gpu(args, rank, world, local_rank):
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# serving loop: Poisson arrivals of full reductions, sizes from the uneven mix
+# ---------------------------------------------------------------------------
+
+SERVE_SIDES = (64, 128, 256, 512, 1024)
+
+
+def serve_requests(seed, n_req, t_range=(16, 400)):
+    """Request shapes and parameters: side from SERVE_SIDES, frame count
+    uniform in t_range, alt-az parallactic angles resampled to the frame
+    count, recentring shifts U(-0.5, 0.5) px, FWHM 4 px, 1.5 FWHM gate."""
+    from paper_1510_04331_gb300 import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_req):
+        n = int(rng.choice(SERVE_SIDES))
+        T = int(rng.integers(t_range[0], t_range[1] + 1))
+        out.append(dict(n=n, T=T, dx=rng.uniform(-0.5, 0.5, T), dy=rng.uniform(-0.5, 0.5, T),
+                        parang=synth.altaz_parang(T), fwhm=4.0, n_fwhm=1.5, edges=synth.default_edges(n)))
+    return out
+
+
+def _pct(v, q):
+    s = sorted(v)
+    return s[min(len(s) - 1, max(0, int(math.ceil(q * len(s))) - 1))]
+
+
+def run_serving(local_rank, n_req=200, rates=(20.0, 200.0, 2000.0), seed=4, max_active=64):
+    """Each rate: the same Poisson arrival sequence served (a) by the serving
+    loop (graphic_server: admission by device memory, cross-request
+    batching) and (b) by plain sequential per-request reductions
+    (graphic_reduce_host in arrival order).  Latency = completion - arrival."""
+    import queue as _queue
+
+    import torch
+    from paper_1510_04331_gb300 import graphic
+
+    reqs = serve_requests(seed, n_req)
+    tmax = max(r["T"] for r in reqs)
+    gen = torch.Generator().manual_seed(seed)
+    pool = {}
+    for n in sorted({r["n"] for r in reqs}):
+        pool[n] = torch.randn((tmax, n, n), generator=gen, dtype=torch.float32).pin_memory()
+    inputs = [pool[r["n"]][:r["T"]] for r in reqs]
+    frames = sum(r["T"] for r in reqs)
+    in_bytes = sum(r["T"] * r["n"] * r["n"] * 4 for r in reqs)
+    results = []
+    for rate in rates:
+        arr = np.cumsum(np.random.default_rng(seed + int(rate)).exponential(1.0 / rate, n_req))
+        row = {"rate_per_s": rate}
+        # (a) serving loop
+        with graphic.Server(local_rank, max_active=max_active) as srv:
+            for r, x in list(zip(reqs, inputs))[:3]:    # warm-up: graphs, plans
+                srv.wait(srv.submit(x, r["dx"], r["dy"], r["parang"], r["fwhm"], r["n_fwhm"], r["edges"]))
+            ids = [None] * n_req
+            ready = threading.Event()
+
+            def submitter():
+                t0 = time.perf_counter()
+                for i, (r, x) in enumerate(zip(reqs, inputs)):
+                    dt = t0 + arr[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    ids[i] = srv.submit(x, r["dx"], r["dy"], r["parang"], r["fwhm"], r["n_fwhm"], r["edges"])
+                ready.set()
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            infos = []
+            for i in range(n_req):
+                while ids[i] is None:
+                    time.sleep(0.0002)
+                infos.append(srv.wait(ids[i])[1])
+            th.join()
+            st = srv.stats()
+        bad = [x for x in infos if x["status"] != 0]
+        lat = [(x["t_done"] - x["t_submit"]) * 1e3 for x in infos]
+        span = max(x["t_done"] for x in infos) - min(x["t_submit"] for x in infos)
+        row["server"] = {"frames_per_s": frames / span, "p50_ms": statistics.median(lat), "p99_ms": _pct(lat, 0.99),
+                         "span_s": span, "failed": len(bad),
+                         "mean_batch": st["batch_items"] / max(1, st["batch_launches"]),
+                         "max_batch": st["max_batch_items"], "max_resident": st["max_resident"],
+                         "iterations": st["iterations"], "device_bytes_peak": st["device_bytes_peak"]}
+        # (b) sequential per-request reductions in arrival order
+        ctx = graphic.Context(local_rank)
+        outs = {n: torch.empty((n, n), dtype=torch.float32).pin_memory() for n in pool}
+        for r, x in list(zip(reqs, inputs))[:3]:
+            ctx.graphic_reduce_host(x, r["dx"], r["dy"], r["parang"], r["fwhm"], r["n_fwhm"], r["edges"],
+                                    out_host=outs[r["n"]])
+        q = _queue.Queue()
+        t_arr = [0.0] * n_req
+        t_done = [0.0] * n_req
+
+        def worker():
+            while True:
+                i = q.get()
+                if i is None:
+                    return
+                r = reqs[i]
+                ctx.graphic_reduce_host(inputs[i], r["dx"], r["dy"], r["parang"], r["fwhm"], r["n_fwhm"],
+                                        r["edges"], out_host=outs[r["n"]])
+                t_done[i] = time.perf_counter()
+
+        wt = threading.Thread(target=worker)
+        wt.start()
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            dt = t0 + arr[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            t_arr[i] = time.perf_counter()
+            q.put(i)
+        q.put(None)
+        wt.join()
+        ctx.close()
+        lat = [(t_done[i] - t_arr[i]) * 1e3 for i in range(n_req)]
+        span = max(t_done) - min(t_arr)
+        row["sequential"] = {"frames_per_s": frames / span, "p50_ms": statistics.median(lat),
+                             "p99_ms": _pct(lat, 0.99), "span_s": span}
+        row["speedup_frames_per_s"] = row["server"]["frames_per_s"] / row["sequential"]["frames_per_s"]
+        results.append(row)
+    return {"requests": n_req, "frames": frames, "input_bytes": in_bytes, "seed": seed, "max_active": max_active,
+            "mix": "sides from {64,128,256,512,1024}, 16-400 frames (seeded), alt-az angles resampled per request, "
+                   "full reduce each (shift, median PSF subtraction, derotation, collapse)",
+            "host_inputs": "pinned host memory, copied in and the result copied out inside each request",
+            "rates": results}
 
 
 # ---------------------------------------------------------------------------
@@ -450,7 +582,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven"])
+    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven", "serve"])
     ap.add_argument("--no-tune", action="store_true", help="uneven workload: skip the autotuner")
     ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
@@ -458,6 +590,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0, help="seconds of oracle work per sample")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-max-active", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -468,6 +603,20 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "uneven":
         return run_uneven(args, rank, world, local_rank)
+    if args.workload == "serve":
+        import torch
+        torch.cuda.set_device(local_rank)
+        sv = run_serving(local_rank, n_req=args.serve_requests, max_active=args.serve_max_active)
+        top = sv["rates"][-1]
+        line = {"metric": "frames/s, serving loop (full reduction requests)", "value": top["server"]["frames_per_s"],
+                "unit": "frames/s", "n_gpus": world, "steps": 1, "warmup": 3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "serving: %d requests, Poisson arrivals, rates %s req/s" %
+                                       (sv["requests"], [r["rate_per_s"] for r in sv["rates"]])},
+                "serving": sv}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -60,6 +60,7 @@ struct graphic_ctx {
   int group_budget_mb = 128;        // grouped executor: scratch of one wave
   int group_streams = 2;            // grouped executor: concurrent graph branches
   int batch_mode = GRAPHIC_BATCH_GROUPED;   // GRAPHIC_BATCH_AUTO resolves to this
+  bool group_graph = true;          // grouped executor: record a graph (false: launch directly)
   // grouped executor state
   float *d_gscratch = nullptr;
   size_t gscratch_bytes = 0;
@@ -217,8 +218,10 @@ long long chunk_frames(const graphic_ctx *c, long long T, size_t bytes_per_frame
   return k;
 }
 
+}  // namespace
+
 // --- shift ------------------------------------------------------------------
-int validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
+int graphic::validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
   if (T > 0 && (!dx || !dy)) return fail(GRAPHIC_ERR_INVALID_ARG, "null dx/dy");
   for (int64_t t = 0; t < T; t++) {
     if (!isfinite(dx[t]) || !isfinite(dy[t])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite shift");
@@ -226,6 +229,8 @@ int validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
   }
   return GRAPHIC_OK;
 }
+
+namespace {
 
 // Enqueue the two shift passes for frames [0, T) with parameters at device
 // pointers p_dx, p_dy.  in -> out (out may equal in).
@@ -329,8 +334,10 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
   return GRAPHIC_OK;
 }
 
+}  // namespace
+
 // --- adi --------------------------------------------------------------------
-int validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+int graphic::validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
   if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
   if (T > GRAPHIC_MAX_FRAMES_MEDIAN) return fail(GRAPHIC_ERR_UNSUPPORTED, "n_frames > GRAPHIC_MAX_FRAMES_MEDIAN");
   if (!parang) return fail(GRAPHIC_ERR_INVALID_ARG, "null parang");
@@ -346,19 +353,11 @@ int validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, co
   return GRAPHIC_OK;
 }
 
-struct AdiPlanHost {
-  std::vector<int> perm;
-  std::vector<int> lr;      // [A][T][2]
-  std::vector<double> edge2;
-  std::vector<int> band;    // [A][4]
-  int wmax = 0;
-};
-
 // Band of full ranks that holds every median annulus `lr` needs: query s has
 // |S| = L + T - R members, its (lower) median is the k-th of S, k = (|S|-1)/2,
 // and at most w = R - L frames are excluded, so that element has full rank in
 // [k, k + w]; with the upper median of an even |S|, in [k, k + 1 + w].
-void plan_band(const int *lr, int64_t T, int *out) {
+static void plan_band(const int *lr, int64_t T, int *out) {
   int64_t blo = T, bhi = -1;
   for (int64_t s = 0; s < T; s++) {
     const int64_t L = lr[2 * s], R = lr[2 * s + 1];
@@ -381,14 +380,14 @@ void plan_band(const int *lr, int64_t T, int *out) {
   out[3] = 0;
 }
 
-double alpha_min_deg(double fwhm, double n_fwhm, double r) {
+static double alpha_min_deg(double fwhm, double n_fwhm, double r) {
   double arg = n_fwhm * fwhm / (2.0 * r);
   if (!(arg < 1.0)) arg = 1.0;
   return 2.0 * asin(arg) * 180.0 / kPi;
 }
 
-void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
-              AdiPlanHost &ap) {
+void graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges,
+                       int32_t n_edges, AdiPlanHost &ap) {
   const int A = n_edges - 1;
   ap.perm.resize(T);
   for (int64_t t = 0; t < T; t++) ap.perm[t] = (int)t;
@@ -450,6 +449,8 @@ void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const
     ap.wmax = std::max(ap.wmax, ap.band[4 * a + 2]);
   }
 }
+
+namespace {
 
 int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
                 const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann) {
@@ -857,25 +858,23 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
     key.push_back(w.mask);
     key.push_back(w.nf);
   }
-  if (c->gexec && key != c->gkey) drop_group_graph(c);
-  if (!c->gexec) {
-    while ((int)c->gstreams.size() < R) {
-      cudaStream_t st;
-      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-      c->gstreams.push_back(st);
-      cudaEvent_t ev;
-      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      c->gevents.push_back(ev);
-    }
-    cudaStream_t s0 = c->gstreams[0];
-    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_plan, c->h_plan, pb.buf.size(), cudaMemcpyHostToDevice, s0);
-    if (e == cudaSuccess) e = cudaEventRecord(c->gevents[0], s0);
+  while ((int)c->gstreams.size() < R) {
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    c->gstreams.push_back(st);
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    c->gevents.push_back(ev);
+  }
+  // the waves on R branches forked from and joined back into `s0`
+  auto enqueue = [&](cudaStream_t s0) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(c->d_plan, c->h_plan, pb.buf.size(), cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess && R > 1) e = cudaEventRecord(c->gevents[0], s0);
     for (int r = 1; r < R && e == cudaSuccess; r++) e = cudaStreamWaitEvent(c->gstreams[r], c->gevents[0], 0);
     for (size_t wi = 0; wi < waves.size() && e == cudaSuccess; wi++) {
       const GroupWave &w = waves[wi];
       const int r = (int)(wi % R);
-      cudaStream_t st = c->gstreams[r];
+      cudaStream_t st = r ? c->gstreams[r] : s0;
       const long long NM = 2ll * w.n * w.n;
       LineArgs a{};
       a.status = c->d_status;
@@ -914,6 +913,21 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
       e = cudaEventRecord(c->gevents[r], c->gstreams[r]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->gevents[r], 0);
     }
+    return e;
+  };
+  if (!c->group_graph) {
+    // direct launches (a layout that changes every call gains nothing from a graph)
+    prof_begin(c, GRAPHIC_K_BATCH);
+    cudaError_t e = enqueue(c->stream);
+    prof_end(c);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped batch launches");
+    return GRAPHIC_OK;
+  }
+  if (c->gexec && key != c->gkey) drop_group_graph(c);
+  if (!c->gexec) {
+    cudaStream_t s0 = c->gstreams[0];
+    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = enqueue(s0);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s0, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1033,6 +1047,37 @@ int time_batch(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items,
 }  // namespace
 
 int graphic::set_last_error(int code, const char *msg) { return fail(code, msg); }
+
+int graphic::ctx_batch_async(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode) {
+  int rc = validate_batch(items, n_items);
+  if (rc) return rc;
+  if (mode == GRAPHIC_BATCH_AUTO) mode = c->batch_mode;
+  if ((rc = begin_call(c))) return rc;
+  switch (mode) {
+    case GRAPHIC_BATCH_PER_CUBE: return batch_per_cube(c, items, n_items);
+    case GRAPHIC_BATCH_PERSISTENT: return batch_persistent(c, items, n_items);
+    case GRAPHIC_BATCH_GROUPED: return batch_grouped(c, items, n_items);
+  }
+  return fail(GRAPHIC_ERR_INVALID_ARG, "unknown batch mode");
+}
+
+void graphic::ctx_set_graph_batches(graphic_ctx *c, bool on) { c->group_graph = on; }
+
+const int *graphic::ctx_status_async(graphic_ctx *c) {
+  if (cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return nullptr;
+  return c->h_status;
+}
+
+size_t graphic::ctx_workspace_bound(const graphic_ctx *c, int32_t mode) {
+  if (mode == GRAPHIC_BATCH_AUTO) mode = c->batch_mode;
+  const size_t mb = 1ull << 20;
+  size_t ws = 64 * mb;   // plans, tables, counters
+  if (mode == GRAPHIC_BATCH_GROUPED) ws += (size_t)c->group_streams * std::max<size_t>(c->group_budget_mb * mb, 8 * mb);
+  else if (mode == GRAPHIC_BATCH_PERSISTENT) ws += 2 * std::max<size_t>(c->batch_budget_mb * mb, 8 * mb);
+  else ws += std::max<size_t>((size_t)c->chunk_mb * mb * 2, 8 * mb);
+  return ws;
+}
 
 extern "C" {
 

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "../../include/graphic.h"
+
 namespace graphic {
 
 // Line-pass kinds: which lines of which buffer one launch transforms.
@@ -32,6 +36,34 @@ struct LineArgs {
 // Record `msg` as the calling thread's last error (graphic_last_error) and
 // return `code` (capi.cu).
 int set_last_error(int code, const char *msg);
+
+// Host plans and argument checks (capi.cu).
+int validate_shift(const double *dx, const double *dy, int64_t T, int32_t n);
+int validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges);
+// Angle-gated reference sets (Sect. 3.3): frames sorted by parallactic angle
+// (stable), per annulus and sorted position s the set {k : |alpha_k -
+// alpha_s| > alpha_min(r_a)} as sorted-position ranges [0, L) u [R, T),
+// farthest frames when empty, and the rank band of each annulus' medians.
+struct AdiPlanHost {
+  std::vector<int> perm;     // [T]
+  std::vector<int> lr;       // [A][T][2]
+  std::vector<double> edge2; // [A+1]
+  std::vector<int> band;     // [A][4]
+  int wmax = 0;
+};
+void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
+              AdiPlanHost &ap);
+
+// Asynchronous context calls for the serving loop (capi.cu): a batch call on
+// the context's stream without the final synchronisation (the status word is
+// cleared first), the status word's copy to pinned host memory (valid once
+// the stream reaches it), and an upper bound of the device workspace the
+// context's batch calls hold.
+int ctx_batch_async(graphic_ctx *c, const graphic_batch_item *items, int32_t n_items, int32_t mode);
+const int *ctx_status_async(graphic_ctx *c);
+size_t ctx_workspace_bound(const graphic_ctx *c, int32_t mode);
+// Grouped batches: record and replay a graph (default) or launch directly.
+void ctx_set_graph_batches(graphic_ctx *c, bool on);
 
 // Device status bits.
 constexpr int STATUS_NONFINITE = 1;

@@ -51,6 +51,37 @@ class BatchItem(ctypes.Structure):
 MAX_FRAMES_MEDIAN = 2048
 
 
+class ServerConfig(ctypes.Structure):
+    """graphic_server_config of include/graphic_serve.h."""
+    _fields_ = [("device", ctypes.c_int32), ("max_active", ctypes.c_int32), ("batch_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64),
+                ("staging_bytes", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    """graphic_request of include/graphic_serve.h."""
+    _fields_ = [("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("n", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("dx", ctypes.POINTER(ctypes.c_double)), ("dy", ctypes.POINTER(ctypes.c_double)),
+                ("parang", ctypes.POINTER(ctypes.c_double)), ("edges", ctypes.POINTER(ctypes.c_double)),
+                ("fwhm", ctypes.c_double), ("n_fwhm", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    """graphic_request_info of include/graphic_serve.h."""
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+SERVER_STATS = ["submitted", "admitted", "completed", "failed", "iterations", "batch_launches", "batch_items",
+                "max_batch_items", "max_resident", "device_bytes_cap", "device_bytes_peak"]
+
+
+class ServerStats(ctypes.Structure):
+    """graphic_server_stats of include/graphic_serve.h."""
+    _fields_ = [(k, ctypes.c_int64) for k in SERVER_STATS]
+
+
 class GraphicError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -83,6 +114,12 @@ _SIGS = {
     "graphic_kernel_name": [_I32],
     "graphic_rotate_noalloc": [_P, _P, _I64, _I32, _D, _P],
     "graphic_workspace_bytes": [_P, ctypes.POINTER(_I64)],
+    "graphic_server_create": [ctypes.POINTER(_P), ctypes.POINTER(ServerConfig)],
+    "graphic_server_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)],
+    "graphic_server_wait": [_P, _I64, ctypes.c_double, ctypes.POINTER(RequestInfo)],
+    "graphic_server_clock": [_P],
+    "graphic_server_stats_read": [_P, ctypes.POINTER(ServerStats)],
+    "graphic_server_destroy": [_P],
     "graphic_batch_geom": [_P, _P, _I32, _I32],
     "graphic_autotune": [_P, _P, _I32, ctypes.c_char_p, _D],
     "graphic_get_schedule": [_P, ctypes.POINTER(_I32), _I32],
@@ -107,6 +144,7 @@ def lib():
                 fn.restype = ctypes.c_int
             L.graphic_last_error.restype = ctypes.c_char_p
             L.graphic_kernel_name.restype = ctypes.c_char_p
+            L.graphic_server_clock.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -309,6 +347,88 @@ class Context:
 
 
 _ctx = {}
+
+
+class Server:
+    """Serving loop (include/graphic_serve.h): full reductions of host cubes
+    submitted by any thread, admitted by device memory and batched across
+    requests on the GPU.  ``submit`` returns a request id; ``wait`` returns
+    (result n x n float32 array, info dict with status and server-clock
+    times).  The host cube must stay alive and unchanged until its request
+    is waited for (pinned memory makes its copy asynchronous)."""
+
+    def __init__(self, device=0, max_active=0, batch_mode=BATCH_GROUPED, max_device_bytes=0, staging_bytes=0):
+        cfg = ServerConfig(int(device), int(max_active), int(batch_mode), 0, int(max_device_bytes),
+                           int(staging_bytes))
+        h = _P()
+        _check(lib().graphic_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self.h = h
+        self._keep = {}
+        self._klock = threading.Lock()
+
+    def submit(self, cube_host, dx, dy, parang, fwhm, n_fwhm, edges, out_host=None):
+        if hasattr(cube_host, "data_ptr"):
+            if cube_host.is_cuda or not cube_host.is_contiguous() or str(cube_host.dtype) != "torch.float32":
+                raise GraphicError(-1, "cube must be a contiguous float32 host tensor")
+            T, n = int(cube_host.shape[0]), int(cube_host.shape[1])
+            ptr = cube_host.data_ptr()
+        else:
+            cube_host = np.ascontiguousarray(cube_host, dtype=np.float32)
+            T, n = cube_host.shape[0], cube_host.shape[1]
+            ptr = cube_host.ctypes.data
+        if len(cube_host.shape) != 3 or cube_host.shape[1] != cube_host.shape[2]:
+            raise GraphicError(-1, "cube must have shape (T, n, n)")
+        if out_host is None:
+            out_host = np.empty((n, n), np.float32)
+        if tuple(out_host.shape) != (n, n):
+            raise GraphicError(-1, "out must have shape (n, n)")
+        optr = out_host.data_ptr() if hasattr(out_host, "data_ptr") else out_host.ctypes.data
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        paa, ppa = _f64(parang, T)
+        ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
+        rq = Request(ptr, optr, T, n, ea.size, pdx, pdy, ppa, ea.ctypes.data_as(_D), float(fwhm), float(n_fwhm))
+        rid = _I64()
+        _check(lib().graphic_server_submit(self.h, ctypes.byref(rq), ctypes.byref(rid)))
+        with self._klock:
+            self._keep[rid.value] = (cube_host, out_host)
+        return rid.value
+
+    def wait(self, rid, timeout=None):
+        info = RequestInfo()
+        _check(lib().graphic_server_wait(self.h, int(rid), -1.0 if timeout is None else float(timeout),
+                                         ctypes.byref(info)))
+        with self._klock:
+            _, out = self._keep.pop(int(rid))
+        d = {"status": info.status, "t_submit": info.t_submit, "t_admit": info.t_admit, "t_done": info.t_done}
+        if info.status != GRAPHIC_OK:
+            d["error"] = f"{ERRORS.get(info.status, info.status)}: {lib().graphic_last_error().decode()}"
+        return out, d
+
+    def clock(self):
+        return lib().graphic_server_clock(self.h)
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().graphic_server_stats_read(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k in SERVER_STATS}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().graphic_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def context(device=None) -> Context:
