@@ -1,20 +1,25 @@
 """The C-ABI library builds, loads without a GPU and exports every function
-declared in include/graphic.h; the host-side argument checks answer before
-any device work.  CPU only (no compute call needs a GPU here)."""
+declared in include/*.h; the host-side argument checks answer before any
+device work; the binding's ctypes structures have the C layout.  CPU only
+(no compute call needs a GPU here)."""
 import ctypes
+import glob
 import os
 import re
+import subprocess
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "graphic.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(graphic_\w+)\s*\(", src, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(graphic_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -47,3 +52,38 @@ def test_host_side_checks_without_gpu(lib):
     assert lib.graphic_kernel_name(0) == b"shift_x"
     assert lib.graphic_kernel_name(99) is None
     assert graphic.KERNELS == [lib.graphic_kernel_name(k).decode() for k in range(len(graphic.KERNELS))]
+
+
+def test_server_host_side_checks_without_gpu(lib):
+    assert lib.graphic_server_create(None, None) == -1
+    assert lib.graphic_server_submit(None, None, None) == -1
+    assert lib.graphic_server_wait(None, 1, 0.0, None) == -1
+    assert lib.graphic_server_stats_read(None, None) == -1
+    assert lib.graphic_server_destroy(None) == 0
+    assert lib.graphic_server_clock(None) == 0.0
+
+
+def test_binding_structures_match_the_c_layout(tmp_path):
+    """sizeof and field offsets of every struct the binding mirrors, from a
+    C program compiled against the headers."""
+    from paper_1510_04331_gb300 import graphic
+    structs = {"graphic_batch_item": graphic.BatchItem, "graphic_server_config": graphic.ServerConfig,
+               "graphic_request": graphic.Request, "graphic_request_info": graphic.RequestInfo,
+               "graphic_server_stats": graphic.ServerStats}
+    c_names = {"in_": "in"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "graphic_serve.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {c_names.get(f, f)}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
