@@ -234,6 +234,29 @@ int graphic_autotune(graphic_ctx *ctx, const graphic_batch_item *items, int32_t 
 int graphic_get_schedule(graphic_ctx *ctx, int32_t *values, int32_t n);
 int graphic_set_schedule(graphic_ctx *ctx, const int32_t *values, int32_t n);
 
+/* ---- precision variant (tensor cores) --------------------------------------- */
+
+#define GRAPHIC_PREC_FP32 0      /* FP32 radix-16 Stockham kernels (default)                */
+#define GRAPHIC_PREC_BF16X3 1    /* DFT stages as BF16 hi+lo GEMMs, FP32 accumulation       */
+#define GRAPHIC_PREC_FP16X3 2    /* DFT stages as FP16 hi+lo GEMMs, FP32 accumulation       */
+
+/*
+ * Arithmetic of the shift and rotation line passes of this context
+ * (graphic_shift, graphic_rotate, graphic_reduce*, and graphic_batch_geom in
+ * the per-cube and grouped modes) for frames of n = 1024 (2048-point
+ * lines); other sizes keep the FP32 kernels.  With BF16X3 / FP16X3 every
+ * 2048-point DFT runs as three radix stages (16, 16, 8), each one GEMM on
+ * the tensor cores (tcgen05) with operands split into hi + lo parts of the
+ * 16-bit type and the products hi.hi + lo.hi + hi.lo accumulated in FP32;
+ * twiddles, phasors and the FP64 phase-argument reduction are those of the
+ * FP32 path.  Error against the FP64 definition, relative to the frame
+ * peak: about 1e-6 (FP16X3) and 1e-4 (BF16X3) per pass, against ~1e-7 for
+ * FP32 (measured per step by the tests).  The persistent batch mode always
+ * uses FP32.
+ */
+int graphic_set_precision(graphic_ctx *ctx, int32_t precision);
+int graphic_get_precision(graphic_ctx *ctx, int32_t *precision);
+
 /* ---- measurement support ------------------------------------------------ */
 
 /* Kernel identifiers for graphic_profile_read. */

@@ -61,6 +61,7 @@ struct graphic_ctx {
   int group_streams = 2;            // grouped executor: concurrent graph branches
   int batch_mode = GRAPHIC_BATCH_GROUPED;   // GRAPHIC_BATCH_AUTO resolves to this
   bool group_graph = true;          // grouped executor: record a graph (false: launch directly)
+  int precision = GRAPHIC_PREC_FP32;   // line-pass arithmetic for frames of n = 1024
   // grouped executor state
   float *d_gscratch = nullptr;
   size_t gscratch_bytes = 0;
@@ -220,6 +221,15 @@ long long chunk_frames(const graphic_ctx *c, long long T, size_t bytes_per_frame
 
 }  // namespace
 
+// One line pass with the context's arithmetic: the tensor-core DFT stages
+// (BF16 / FP16 hi + lo) where the precision variant asks for them and the
+// frame size has them, else the FP32 kernels.
+cudaError_t line_pass(const graphic_ctx *c, LineKind kind, const LineArgs &a, long long nf, cudaStream_t st) {
+  if (c->precision != GRAPHIC_PREC_FP32 && tc_supported(a.n))
+    return launch_line_pass_tc(kind, a, nf, st, c->precision);
+  return launch_line_pass(kind, a, nf, st, c->variant_1024);
+}
+
 // --- shift ------------------------------------------------------------------
 int graphic::validate_shift(const double *dx, const double *dy, int64_t T, int32_t n) {
   if (T > 0 && (!dx || !dy)) return fail(GRAPHIC_ERR_INVALID_ARG, "null dx/dy");
@@ -250,12 +260,12 @@ int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_
     a.out_fstride = NN;
     a.n = n;
     prof_begin(c, GRAPHIC_K_SHIFT_X);
-    cudaError_t e = launch_line_pass(SHIFT_X, a, nf, c->stream, c->variant_1024);
+    cudaError_t e = line_pass(c, SHIFT_X, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift x pass");
     a.in = out + f0 * NN;
     prof_begin(c, GRAPHIC_K_SHIFT_Y);
-    e = launch_line_pass(SHIFT_Y, a, nf, c->stream, c->variant_1024);
+    e = line_pass(c, SHIFT_Y, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift y pass");
   }
@@ -311,7 +321,7 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.in_fstride = NN;
     a.out_fstride = NM;
     prof_begin(c, GRAPHIC_K_ROT_P1);
-    cudaError_t e = launch_line_pass(ROT_P1, a, nf, c->stream, c->variant_1024);
+    cudaError_t e = line_pass(c, ROT_P1, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 1");
     // pass 2: scratch columns, in place
@@ -320,14 +330,14 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.in_fstride = NM;
     a.out_fstride = NM;
     prof_begin(c, GRAPHIC_K_ROT_P2);
-    e = launch_line_pass(ROT_P2, a, nf, c->stream, c->variant_1024);
+    e = line_pass(c, ROT_P2, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 2");
     // pass 3: scratch rows -> frame rows
     a.out = out + f0 * NN;
     a.out_fstride = NN;
     prof_begin(c, GRAPHIC_K_ROT_P3);
-    e = launch_line_pass(ROT_P3, a, nf, c->stream, c->variant_1024);
+    e = line_pass(c, ROT_P3, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 3");
   }
@@ -851,7 +861,7 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
   memcpy(c->h_plan, pb.buf.data(), pb.buf.size());
   std::vector<long long> key = {(long long)(uintptr_t)c->h_plan, (long long)(uintptr_t)c->d_plan,
                                 (long long)pb.buf.size(), (long long)(uintptr_t)c->d_gscratch, (long long)slot_bytes,
-                                (long long)(uintptr_t)c->d_status, R, c->variant_1024,
+                                (long long)(uintptr_t)c->d_status, R, c->variant_1024, c->precision,
                                 (long long)(uintptr_t)c->stream};
   for (const GroupWave &w : waves) {
     key.push_back(w.n);
@@ -884,9 +894,9 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
         a.out_tab = at<float *>(c, o_out) + w.f0;
         a.p0 = at<double>(c, o_dx) + w.f0;
         a.p1 = at<double>(c, o_dy) + w.f0;
-        e = launch_line_pass(SHIFT_X, a, w.nf, st, c->variant_1024);
+        e = line_pass(c, SHIFT_X, a, w.nf, st);
         a.in_tab = at<const float *>(c, o_out) + w.f0;
-        if (e == cudaSuccess) e = launch_line_pass(SHIFT_Y, a, w.nf, st, c->variant_1024);
+        if (e == cudaSuccess) e = line_pass(c, SHIFT_Y, a, w.nf, st);
       }
       if ((w.mask & GRAPHIC_PASS_ROTATE) && e == cudaSuccess) {
         float *slot = c->d_gscratch + (size_t)r * (slot_bytes / sizeof(float));
@@ -899,14 +909,14 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
         b.in_tab = at<const float *>(c, o_rin) + w.f0;
         b.out = slot;
         b.out_fstride = NM;
-        e = launch_line_pass(ROT_P1, b, w.nf, st, c->variant_1024);
+        e = line_pass(c, ROT_P1, b, w.nf, st);
         b.in_tab = nullptr;
         b.in = slot;
         b.in_fstride = NM;
-        if (e == cudaSuccess) e = launch_line_pass(ROT_P2, b, w.nf, st, c->variant_1024);
+        if (e == cudaSuccess) e = line_pass(c, ROT_P2, b, w.nf, st);
         b.out = nullptr;
         b.out_tab = at<float *>(c, o_out) + w.f0;
-        if (e == cudaSuccess) e = launch_line_pass(ROT_P3, b, w.nf, st, c->variant_1024);
+        if (e == cudaSuccess) e = line_pass(c, ROT_P3, b, w.nf, st);
       }
     }
     for (int r = 1; r < R && e == cudaSuccess; r++) {
@@ -1100,7 +1110,7 @@ int graphic_create(graphic_ctx **out, int device) {
   DeviceGuard g(device);
   graphic_ctx *c = new graphic_ctx();
   c->device = device;
-  if (geom_init_device() != 0) {
+  if (geom_init_device() != 0 || tc_init_device() != 0) {
     delete c;
     return fail(GRAPHIC_ERR_CUDA, "twiddle table upload failed");
   }
@@ -1355,6 +1365,21 @@ int graphic_set_schedule(graphic_ctx *c, const int32_t *values, int32_t n) {
   for (int32_t k = 0; k < n && k < GRAPHIC_SCHEDULE_LEN; k++)
     if (!schedule_value_ok(k, values[k])) return fail(GRAPHIC_ERR_INVALID_ARG, "bad schedule value");
   for (int32_t k = 0; k < n && k < GRAPHIC_SCHEDULE_LEN; k++) *dst[k] = values[k];
+  return GRAPHIC_OK;
+}
+
+int graphic_set_precision(graphic_ctx *c, int32_t precision) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (precision != GRAPHIC_PREC_FP32 && precision != GRAPHIC_PREC_BF16X3 && precision != GRAPHIC_PREC_FP16X3)
+    return fail(GRAPHIC_ERR_INVALID_ARG, "unknown precision");
+  c->precision = precision;
+  drop_group_graph(c);   // recorded launches name the kernels
+  return GRAPHIC_OK;
+}
+
+int graphic_get_precision(graphic_ctx *c, int32_t *precision) {
+  if (!c || !precision) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  *precision = c->precision;
   return GRAPHIC_OK;
 }
 

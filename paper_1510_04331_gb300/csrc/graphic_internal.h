@@ -112,6 +112,16 @@ struct BatchArgs {
 };
 cudaError_t launch_batch_persistent(const BatchArgs &b, int ctas_per_sm, cudaStream_t st);
 
+// tc.cu: line passes with the DFT stages on the tensor cores (frames of
+// n = 1024 only), operands split into hi + lo parts of BF16 or FP16.
+constexpr int PREC_FP32 = 0;
+constexpr int PREC_BF16X3 = 1;
+constexpr int PREC_FP16X3 = 2;
+int tc_init_device();      // twiddles and DFT operand tables of the current device (0 = ok)
+bool tc_supported(int n);
+cudaError_t launch_line_pass_tc(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st,
+                                int precision);
+
 // median.cu
 struct AdiArgs {
   const float *in;

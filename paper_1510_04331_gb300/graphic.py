@@ -36,6 +36,9 @@ BATCH_PER_CUBE = 0
 BATCH_PERSISTENT = 1
 BATCH_GROUPED = 2
 BATCH_AUTO = 3
+PREC_FP32 = 0
+PREC_BF16X3 = 1
+PREC_FP16X3 = 2
 PASS_SHIFT = 1
 PASS_ROTATE = 2
 SCHEDULE_KEYS = ["chunk_mb", "variant_1024", "batch_budget_mb", "batch_ctas_per_sm", "group_budget_mb",
@@ -114,6 +117,8 @@ _SIGS = {
     "graphic_kernel_name": [_I32],
     "graphic_rotate_noalloc": [_P, _P, _I64, _I32, _D, _P],
     "graphic_workspace_bytes": [_P, ctypes.POINTER(_I64)],
+    "graphic_set_precision": [_P, _I32],
+    "graphic_get_precision": [_P, ctypes.POINTER(_I32)],
     "graphic_server_create": [ctypes.POINTER(_P), ctypes.POINTER(ServerConfig)],
     "graphic_server_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)],
     "graphic_server_wait": [_P, _I64, ctypes.c_double, ctypes.POINTER(RequestInfo)],
@@ -326,6 +331,16 @@ class Context:
         k = len(SCHEDULE_KEYS)
         v = (_I32 * k)(*[int(cur[key]) for key in SCHEDULE_KEYS])
         _check(lib().graphic_set_schedule(self.h, v, k))
+
+    def set_precision(self, precision: int):
+        """PREC_FP32 (default), PREC_BF16X3 or PREC_FP16X3: arithmetic of the
+        line passes for frames of n = 1024 (tensor-core DFT stages)."""
+        _check(lib().graphic_set_precision(self.h, int(precision)))
+
+    def precision(self) -> int:
+        v = _I32()
+        _check(lib().graphic_get_precision(self.h, ctypes.byref(v)))
+        return v.value
 
     def profile(self, enable: bool):
         _check(lib().graphic_profile(self.h, int(bool(enable))))
