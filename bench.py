@@ -66,6 +66,24 @@ def workload_desc(name, d):
     return f"{T} frames of {n}x{n} (padded to {2 * n}), {name} recipe; full reduce"
 
 
+def max_over_ranks(value, device=None):
+    """Max of a float over all ranks of the default process group (the value
+    itself without one, or at world size 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, steps, world, max_ms):
+    """Whole-job throughput: the units all ranks processed / the slowest
+    rank's elapsed time (weak scaling: fixed work per rank)."""
+    return units_per_rank_step * steps * world / (max_ms / 1e3)
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -285,14 +303,8 @@ def run_gpu(args, rank, world, local_rank):
     ctx.profile(False)
     clocks = sampler.stop() if sampler else None
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    frames_total = T * args.steps * world
-    value = frames_total / (total_ms / 1e3)
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dev)
+    value = job_throughput(T, args.steps, world, total_ms)
 
     # e2e: host buffers through graphic_reduce_host, copies inside the timed region
     e2e = None
@@ -306,13 +318,8 @@ def run_gpu(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(ne):
             ctx.graphic_reduce_host(host, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges, out_host=hout)
-        el = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": T * ne * world / el, "unit": "frames/s", "h2d_bytes_per_step": T * NN * 4,
+        el = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": job_throughput(T, ne, world, el * 1e3), "unit": "frames/s", "h2d_bytes_per_step": T * NN * 4,
                "d2h_bytes_per_step": NN * 4, "steps": ne}
 
     if rank != 0:
@@ -378,6 +385,126 @@ def run_gpu(args, rank, world, local_rank):
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# precision variant: 512 frames of 1024 x 1024 (2048-point lines), shift + 3-shear rotation
+# ---------------------------------------------------------------------------
+
+def tc_gemm_flops_per_frame(n=1024):
+    """Tensor-core flops one frame of side n costs in the precision variant:
+    per 2048-point transform two radix-16 stages (128 x 32 x 32) and one
+    radix-8 stage (256 x 16 x 16), three split products each, two
+    transforms (forward, inverse) per line pair."""
+    per_transform = 3 * 2 * (2 * 128 * 32 * 32 + 256 * 16 * 16)
+    pairs = n // 2 * 4 + n   # shift x, shift y, rotation 1, 3 (n / 2 pairs each), rotation 2 (n pairs)
+    return 2 * per_transform * pairs
+
+
+def bf16_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "measured (cuBLAS bf16 burst, MEASURED_PEAKS.json)"
+    except Exception:
+        return 1900.0, "fallback 1.9 PFLOP/s"
+
+
+def run_precision(args, rank, world, local_rank):
+    """Each step: shift then rotate every frame of a 512 x 1024 x 1024 cube
+    (the geometric steps of the reduction at 2048-point lines), once per
+    arithmetic; errors of each step against the FP64 oracle on sampled
+    frames of the survey recipe at this size."""
+    import torch
+    import oracle
+    from paper_1510_04331_gb300 import graphic, synth
+
+    torch.cuda.set_device(local_rank)
+    T, n = (args.frames or 512), 1024
+    gen = torch.Generator(device="cuda").manual_seed(3 + rank)
+    cube = torch.randn((T, n, n), generator=gen, device="cuda")
+    out = torch.empty_like(cube)
+    rng = np.random.default_rng(3)
+    dx, dy = rng.uniform(-0.5, 0.5, T), rng.uniform(-0.5, 0.5, T)
+    th = -synth.altaz_parang(T)
+    names = {graphic.PREC_FP32: "fp32", graphic.PREC_BF16X3: "bf16x3", graphic.PREC_FP16X3: "fp16x3"}
+    res = {}
+    sampler = ClockSampler(gpu_uuid_or_index(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    for prec, name in names.items():
+        ctx = graphic.Context(local_rank)
+        ctx.set_precision(prec)
+
+        def step():
+            ctx.graphic_shift(cube, dx, dy, out=out)
+            ctx.graphic_rotate(out, th, out=out)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        ctx.close()
+        med = statistics.median(ms)
+        kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                for k, v in prof.items() if v[1]}
+        res[name] = {"ms_p50": med, "frames_per_s": T / (med / 1e3), "kernels": kern}
+    clocks = sampler.stop() if sampler else None
+    # per-step error against the FP64 oracle on 2 frames of the survey recipe at n = 1024
+    d = synth.make_cube(2, n, seed=3, parang=synth.altaz_parang(2), peak=1e5, rho=0.99,
+                        edges=synth.default_edges(n))
+    x64 = d.cube.astype(np.float64)
+    ex, ey, et = np.array([0.31, -0.47]), np.array([-0.22, 0.44]), np.array([37.7, -101.3])
+    ref_s = oracle.shift(x64, ex, ey)
+    ref_r = oracle.rotate(ref_s, et)
+    peak_in = float(np.abs(d.cube).max())
+    for prec, name in names.items():
+        ctx = graphic.Context(local_rank)
+        ctx.set_precision(prec)
+        xs = ctx.graphic_shift(torch.from_numpy(d.cube).cuda(), ex, ey)
+        e_s = float(np.abs(xs.cpu().numpy() - ref_s).max() / peak_in)
+        xr = ctx.graphic_rotate(torch.from_numpy(ref_s.astype(np.float32)).cuda(), et)
+        e_r = float(np.abs(xr.cpu().numpy() - ref_r).max() / peak_in)
+        ctx.close()
+        res[name]["error_vs_fp64_oracle"] = {"shift": e_s, "rotate": e_r, "unit": "max abs / frame peak"}
+    tc_flops = tc_gemm_flops_per_frame(n) * T
+    bpk, bsrc = bf16_peak()
+    best_tc = min(("bf16x3", "fp16x3"), key=lambda k: res[k]["ms_p50"])
+    ach = tc_flops / (res[best_tc]["ms_p50"] / 1e3) / 1e12
+    fp32_flops = T * sum(fft_flops_per_frame(k, n) for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2",
+                                                                "rot_pass3"))
+    line = {
+        "metric": "frames/s, 1024x1024 shift + 3-shear rotation (2048-point lines), per arithmetic",
+        "value": res[best_tc]["frames_per_s"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res[best_tc]["ms_p50"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": best_tc, "data": "synthetic",
+        "config": {"workload": f"{T} frames of 1024x1024 padded to 2048, shift U(-0.5,0.5) px + derotation by "
+                               "alt-az angles; errors on 2 frames of the survey recipe (peak 1e5)",
+                   "frames": T, "n": n, "l2": "inputs larger than L2 (%.1f GB)" % (T * n * n * 4 / 1e9)},
+        "variants": res,
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": bpk, "unit": "TFLOP/s", "frac": ach / bpk,
+                     "traffic": None, "kernel": f"line_pass_tc ({best_tc}), GEMM flops executed",
+                     "peak_source": bsrc, "algorithmic_per_launch": tc_flops},
+        "fp32_roofline": {"bound": "alu", "achieved": fp32_flops / (res["fp32"]["ms_p50"] / 1e3) / 1e12,
+                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": fp32_flops / (res["fp32"]["ms_p50"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -582,7 +709,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven", "serve"])
+    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven", "serve", "precision"])
     ap.add_argument("--no-tune", action="store_true", help="uneven workload: skip the autotuner")
     ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
@@ -603,6 +730,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "uneven":
         return run_uneven(args, rank, world, local_rank)
+    if args.workload == "precision":
+        return run_precision(args, rank, world, local_rank)
     if args.workload == "serve":
         import torch
         torch.cuda.set_device(local_rank)
