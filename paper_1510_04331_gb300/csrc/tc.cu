@@ -12,8 +12,9 @@
 //   stage 3  Z[k]         = sum_b2 v[c,b2][c2] W8^(b2 d3)
 // One stage is D[rows x 2R] = A[rows x 2R] . B with rows the independent
 // R-point vectors (128 per line; 256 for the radix-8 stage), complex values
-// split into real and imaginary halves of K, and B the real form of the DFT
-// matrix.  A and B are split into hi + lo parts of one 16-bit type (BF16 or
+// interleaved along K (re, im) -- one packed 32-bit word per complex value
+// and part -- and B the real form of the DFT matrix, its output columns
+// interleaved the same way.  A and B are split into hi + lo parts of one 16-bit type (BF16 or
 // FP16), x = hi + lo 2^-s with lo stored scaled by 2^s (s = 8 for BF16, 11
 // for FP16: the lo parts keep the normal range, which the tensor cores need
 // -- subnormal FP16 operands lose their value), and two FP32 accumulators in
@@ -48,9 +49,15 @@ namespace {
 constexpr int TC_M = 2048;        // padded line length
 constexpr int TC_N = 1024;        // frame side
 constexpr int TC_PPC = 4;         // line pairs per CTA (one after the other)
+#ifndef TC_MIN_CTAS
+#define TC_MIN_CTAS 4             // resident CTAs per SM the register budget is cut for (4: fastest measured)
+#endif
 
-// W_2048^e = exp(-i 2 pi e / 2048) (FP64 cos / sin rounded to FP32).
-__device__ float2 d_tw2048[TC_M];
+// Twiddles (FP64 cos / sin rounded to FP32), laid out for coalesced reads:
+// stage 1 W_2048^(t c) at [c][t] (t < 128, c < 16), stage 2 W_128^(b2 c2)
+// at [b2][c2] (b2 < 8, c2 < 16).
+__device__ float2 d_tw1[16 * 128];
+__device__ float2 d_tw2[8 * 16];
 
 // Real forms of the DFT matrices (B operands, N x K, K-major core-matrix
 // order), hi and lo parts, per element type (0: BF16, 1: FP16).
@@ -75,15 +82,21 @@ constexpr int SM_B8 = 20480;      // radix-8 B hi, lo (512 each)
 constexpr int SM_Z = 21504;       // natural-order spectrum, 2048 x float2
 constexpr int SM_BYTES = SM_Z + TC_M * 8;
 
+// two floats -> one 32-bit word of two 16-bit values (lo half = a), and back
 template <bool F16>
-__device__ __forceinline__ uint16_t to16(float x) {
-  if constexpr (F16) return __half_as_ushort(__float2half_rn(x));
-  else return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if constexpr (F16) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
 }
 template <bool F16>
-__device__ __forceinline__ float from16(uint16_t h) {
-  if constexpr (F16) return __half2float(__ushort_as_half(h));
-  else return __bfloat162float(__ushort_as_bfloat16(h));
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+  if constexpr (F16) return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
 }
 
 // scale of the stored lo parts: 2^(precision bits of the type)
@@ -93,21 +106,28 @@ struct LoScale {
   static constexpr float down = F16 ? (1.f / 2048.f) : (1.f / 256.f);
 };
 
-// x -> (hi, lo 2^s); FP16 values below the normal range go wholly into lo
+// complex x -> packed hi and packed lo 2^s; FP16 values below the normal
+// range go wholly into lo
 template <bool F16>
-__device__ __forceinline__ void split16(float x, uint16_t &h, uint16_t &l) {
-  if constexpr (F16) h = (fabsf(x) < 6.103515625e-05f) ? (uint16_t)0 : to16<true>(x);
-  else h = to16<false>(x);
-  l = to16<F16>((x - from16<F16>(h)) * LoScale<F16>::up);
+__device__ __forceinline__ void split2(float2 x, uint32_t &h, uint32_t &l) {
+  h = pack2<F16>(x.x, x.y);
+  float2 hf = unpack2<F16>(h);
+  if constexpr (F16) {
+    const bool tr = fabsf(x.x) < 6.103515625e-05f, ti = fabsf(x.y) < 6.103515625e-05f;
+    h &= (tr ? 0xffff0000u : 0xffffffffu) & (ti ? 0x0000ffffu : 0xffffffffu);
+    hf.x = tr ? 0.f : hf.x;
+    hf.y = ti ? 0.f : hf.y;
+  }
+  l = pack2<F16>((x.x - hf.x) * LoScale<F16>::up, (x.y - hf.y) * LoScale<F16>::up);
 }
 
-// value x -> hi and lo parts at byte offset `off` of the A operand
+// complex x -> hi and lo words at byte offset `off` of the A operand
 template <bool F16>
-__device__ __forceinline__ void put_split(unsigned char *sm, int off, float x) {
-  uint16_t h, l;
-  split16<F16>(x, h, l);
-  *reinterpret_cast<uint16_t *>(sm + SM_A + off) = h;
-  *reinterpret_cast<uint16_t *>(sm + SM_ALO + off) = l;
+__device__ __forceinline__ void put_split(unsigned char *sm, int off, float2 x) {
+  uint32_t h, l;
+  split2<F16>(x, h, l);
+  *reinterpret_cast<uint32_t *>(sm + SM_A + off) = h;
+  *reinterpret_cast<uint32_t *>(sm + SM_ALO + off) = l;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -262,8 +282,8 @@ __device__ __forceinline__ void run_stage(TcState &s) {
 }
 
 // Forward 2048-point DFT of the line whose stage-1 operand is in place.
-// On return, thread t holds Z[t + 256 d3] in w[d3] (re) / w[8 + d3] (im)
-// and Z[128 + t + 256 d3] in w[16 + d3] / w[24 + d3].
+// On return, thread t holds Z[t + 256 d3] in (w[2 d3], w[2 d3 + 1]) and
+// Z[128 + t + 256 d3] in (w[16 + 2 d3], w[17 + 2 d3]).
 template <bool F16>
 __device__ __forceinline__ void dft2048(TcState &s, float (&w)[32]) {
   const int t = s.tid;
@@ -275,10 +295,8 @@ __device__ __forceinline__ void dft2048(TcState &s, float (&w)[32]) {
     const int a2 = t >> 3, b2 = t & 7;
 #pragma unroll
     for (int c = 0; c < 16; c++) {
-      const float2 x = cmul(make_float2(u[c], u[16 + c]), __ldg(&d_tw2048[(t * c) & (TC_M - 1)]));
-      const int r = c * 8 + b2;
-      put_split<F16>(s.sm, kmaj_off(r, a2, 32), x.x);
-      put_split<F16>(s.sm, kmaj_off(r, 16 + a2, 32), x.y);
+      const float2 x = cmul(make_float2(u[2 * c], u[2 * c + 1]), __ldg(&d_tw1[c * 128 + t]));
+      put_split<F16>(s.sm, kmaj_off(c * 8 + b2, 2 * a2, 32), x);
     }
   }
   to_mma_sync();
@@ -290,10 +308,8 @@ __device__ __forceinline__ void dft2048(TcState &s, float (&w)[32]) {
     const int c = t >> 3, b2 = t & 7;
 #pragma unroll
     for (int c2 = 0; c2 < 16; c2++) {
-      const float2 x = cmul(make_float2(v[c2], v[16 + c2]), __ldg(&d_tw2048[(16 * b2 * c2) & (TC_M - 1)]));
-      const int r3 = 16 * c2 + c;
-      put_split<F16>(s.sm, kmaj_off(r3, b2, 16), x.x);
-      put_split<F16>(s.sm, kmaj_off(r3, 8 + b2, 16), x.y);
+      const float2 x = cmul(make_float2(v[2 * c2], v[2 * c2 + 1]), __ldg(&d_tw2[b2 * 16 + c2]));
+      put_split<F16>(s.sm, kmaj_off(16 * c2 + c, 2 * b2, 16), x);
     }
   }
   to_mma_sync();
@@ -302,24 +318,13 @@ __device__ __forceinline__ void dft2048(TcState &s, float (&w)[32]) {
   acc_row<F16>(s.tmem_row, w);
 }
 
-// Stage-1 operand row b = t from the natural-order values z[128 a + t].
+// Stage-1 operand row b = t from the natural-order values z[128 a + t]:
+// complex value a at K positions (2a, 2a + 1), written as 16-byte chunks.
 template <bool F16>
 __device__ __forceinline__ void put_row_s1(unsigned char *sm, int t, const float2 (&z)[16]) {
-  // 16 complex values -> K positions a (re) and 16 + a (im) of row t, as 16-byte chunks
   uint32_t hw[16], lw[16];
 #pragma unroll
-  for (int h = 0; h < 2; h++) {       // h = 0: real parts, 1: imaginary parts
-#pragma unroll
-    for (int i = 0; i < 8; i++) {     // K pairs (2i, 2i + 1) of this half
-      const float x0 = h ? z[2 * i].y : z[2 * i].x;
-      const float x1 = h ? z[2 * i + 1].y : z[2 * i + 1].x;
-      uint16_t h0, h1, l0, l1;
-      split16<F16>(x0, h0, l0);
-      split16<F16>(x1, h1, l1);
-      hw[8 * h + i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-      lw[8 * h + i] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-    }
-  }
+  for (int a = 0; a < 16; a++) split2<F16>(z[a], hw[a], lw[a]);
 #pragma unroll
   for (int q = 0; q < 4; q++) {       // four 8-element core-matrix rows along K
     const int off = kmaj_off(t, 8 * q, 32);
@@ -330,7 +335,7 @@ __device__ __forceinline__ void put_row_s1(unsigned char *sm, int t, const float
 }
 
 template <int KIND, bool F16>
-__global__ void __launch_bounds__(128, 4) line_pass_tc(const LineArgs a) {
+__global__ void __launch_bounds__(128, TC_MIN_CTAS) line_pass_tc(const LineArgs a) {
   constexpr int M = TC_M, N = TC_N;
   constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
   constexpr int NIN = (KIND == ROT_P3) ? M : N;
@@ -476,8 +481,8 @@ __global__ void __launch_bounds__(128, 4) line_pass_tc(const LineArgs a) {
     dft2048<F16>(st, w);
 #pragma unroll
     for (int d3 = 0; d3 < 8; d3++) {
-      Z[tid + 256 * d3] = make_float2(w[d3], w[8 + d3]);
-      Z[128 + tid + 256 * d3] = make_float2(w[16 + d3], w[24 + d3]);
+      Z[tid + 256 * d3] = make_float2(w[2 * d3], w[2 * d3 + 1]);
+      Z[128 + tid + 256 * d3] = make_float2(w[16 + 2 * d3], w[17 + 2 * d3]);
     }
     __syncthreads();
 
@@ -530,7 +535,7 @@ __global__ void __launch_bounds__(128, 4) line_pass_tc(const LineArgs a) {
       for (int d3 = 0; d3 < 8; d3++) {
         const int pos = 128 * tt + tid + 256 * d3;
         if (256 * d3 < NOUT) {
-          const float2 y = make_float2(w[16 * tt + d3] * sc_out, -w[16 * tt + 8 + d3] * sc_out);
+          const float2 y = make_float2(w[16 * tt + 2 * d3] * sc_out, -w[16 * tt + 2 * d3 + 1] * sc_out);
           if constexpr (KIND == SHIFT_Y) {
             *reinterpret_cast<float2 *>(fout + (size_t)pos * N + line0) = y;
           } else if constexpr (KIND == ROT_P2) {
@@ -601,20 +606,20 @@ float host_from16(uint16_t h, bool f16) {
   return __bfloat162float(__ushort_as_bfloat16(h));
 }
 
-// B[n][k] of a radix-R stage: y_c = sum_a x_a W_R^(a c), complex values as
-// (re[0..R), im[0..R)):  B[c][a] = Re W, B[c][R+a] = -Im W, B[R+c][a] = Im W,
-// B[R+c][R+a] = Re W.
+// B[n][k] of a radix-R stage: y_c = sum_a x_a W_R^(a c), complex values
+// interleaved (re, im):  B[2c][2a] = Re W, B[2c][2a+1] = -Im W,
+// B[2c+1][2a] = Im W, B[2c+1][2a+1] = Re W.
 void fill_dft(int R, bool f16, uint16_t *hi, uint16_t *lo) {
   const double pi = 3.14159265358979323846;
   const int K = 2 * R;
   for (int n = 0; n < K; n++)
     for (int k = 0; k < K; k++) {
-      const int c = n % R, a = k % R;
+      const int c = n >> 1, a = k >> 1;
       const double ang = 2.0 * pi * (double)((a * c) % R) / (double)R;
       const double wr = cos(ang), wi = -sin(ang);
       double v;
-      if (n < R) v = (k < R) ? wr : -wi;
-      else v = (k < R) ? wi : wr;
+      if ((n & 1) == 0) v = (k & 1) ? -wi : wr;
+      else v = (k & 1) ? wr : wi;
       const uint16_t h = (f16 && fabs(v) < 6.103515625e-05) ? (uint16_t)0 : host16((float)v, f16);
       const uint16_t l = host16((float)((v - (double)host_from16(h, f16)) * (f16 ? 2048.0 : 256.0)), f16);
       const int idx = kmaj_off(n, k, K) / 2;
@@ -626,21 +631,29 @@ void fill_dft(int R, bool f16, uint16_t *hi, uint16_t *lo) {
 }  // namespace
 
 int tc_init_device() {
-  static float2 tw[TC_M];
+  static float2 tw1[16 * 128], tw2[8 * 16];
   static TcTables tab;
   static bool filled = false;
   if (!filled) {
-    for (int e = 0; e < TC_M; e++) {
-      const double ang = 2.0 * 3.14159265358979323846 * (double)e / (double)TC_M;
-      tw[e] = make_float2((float)cos(ang), (float)-sin(ang));
-    }
+    const double pi = 3.14159265358979323846;
+    for (int c = 0; c < 16; c++)
+      for (int t = 0; t < 128; t++) {
+        const double ang = 2.0 * pi * (double)((t * c) % TC_M) / (double)TC_M;
+        tw1[c * 128 + t] = make_float2((float)cos(ang), (float)-sin(ang));
+      }
+    for (int b2 = 0; b2 < 8; b2++)
+      for (int c2 = 0; c2 < 16; c2++) {
+        const double ang = 2.0 * pi * (double)((b2 * c2) % 128) / 128.0;
+        tw2[b2 * 16 + c2] = make_float2((float)cos(ang), (float)-sin(ang));
+      }
     for (int ty = 0; ty < 2; ty++) {
       fill_dft(16, ty == 1, tab.r16[ty][0], tab.r16[ty][1]);
       fill_dft(8, ty == 1, tab.r8[ty][0], tab.r8[ty][1]);
     }
     filled = true;
   }
-  if (cudaMemcpyToSymbol(d_tw2048, tw, sizeof(tw)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(d_tw1, tw1, sizeof(tw1)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(d_tw2, tw2, sizeof(tw2)) != cudaSuccess) return -1;
   if (cudaMemcpyToSymbol(d_tc, &tab, sizeof(tab)) != cudaSuccess) return -1;
   return 0;
 }
