@@ -62,6 +62,9 @@ struct graphic_ctx {
   int batch_mode = GRAPHIC_BATCH_GROUPED;   // GRAPHIC_BATCH_AUTO resolves to this
   bool group_graph = true;          // grouped executor: record a graph (false: launch directly)
   int precision = GRAPHIC_PREC_FP32;   // line-pass arithmetic for frames of n = 1024
+  // graphic_reduce_host: copy stream and event (cube copied in chunks ahead of the shift pass)
+  cudaStream_t s_copy = nullptr;
+  cudaEvent_t ev_copy = nullptr;
   // grouped executor state
   float *d_gscratch = nullptr;
   size_t gscratch_bytes = 0;
@@ -502,9 +505,12 @@ const T *at(const graphic_ctx *c, size_t off) {
   return reinterpret_cast<const T *>(c->d_plan + off);
 }
 
+// Full reduction of the device cube `in` (work may equal in).  With host_in,
+// `in` is first filled from host_in, chunk by chunk on the context's copy
+// stream, each chunk's shift pass starting as soon as its copy is done.
 int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
-                  int32_t n_edges, float *out) {
+                  int32_t n_edges, float *out, const float *host_in = nullptr) {
   int rc = validate_shift(dx, dy, T, n);
   if (rc) return rc;
   rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges);
@@ -526,7 +532,29 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
-  if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
+  if (!host_in) {
+    if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
+  } else {
+    if (!c->s_copy) {
+      CK(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming));
+    }
+    // the copies start after everything already on the compute stream
+    CK(cudaEventRecord(c->ev_copy, c->stream));
+    CK(cudaStreamWaitEvent(c->s_copy, c->ev_copy, 0));
+    const size_t NN = (size_t)n * n;
+    const long long ch = chunk_frames(c, T, NN * sizeof(float));
+    for (long long f0 = 0; f0 < T; f0 += ch) {
+      const long long nf = std::min<long long>(ch, T - f0);
+      CK(cudaMemcpyAsync(const_cast<float *>(in) + f0 * NN, host_in + f0 * NN, nf * NN * sizeof(float),
+                         cudaMemcpyHostToDevice, c->s_copy));
+      CK(cudaEventRecord(c->ev_copy, c->s_copy));
+      CK(cudaStreamWaitEvent(c->stream, c->ev_copy, 0));
+      if ((rc = enqueue_shift(c, in + f0 * NN, work + f0 * NN, nf, n, at<double>(c, o_dx) + f0,
+                              at<double>(c, o_dy) + f0)))
+        return rc;
+    }
+  }
   if ((rc = enqueue_adi(c, work, work, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
                         at<int>(c, o_band), ap.wmax, n_edges - 1)))
     return rc;
@@ -1163,6 +1191,8 @@ int graphic_destroy(graphic_ctx *c) {
   cudaFreeHost(c->h_status);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (cudaEvent_t e : c->gevents) cudaEventDestroy(e);
+  if (c->ev_copy) cudaEventDestroy(c->ev_copy);
+  if (c->s_copy) cudaStreamDestroy(c->s_copy);
   for (cudaStream_t st : c->gstreams) cudaStreamDestroy(st);
   delete c;
   return GRAPHIC_OK;
@@ -1270,8 +1300,8 @@ int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t
   const size_t NN = (size_t)n * n;
   if ((rc = ensure((void **)&c->d_cube, &c->cube_bytes, (size_t)T * NN * sizeof(float), false))) return rc;
   if ((rc = ensure((void **)&c->d_img, &c->img_bytes, NN * sizeof(float), false))) return rc;
-  CK(cudaMemcpyAsync(c->d_cube, host_in, (size_t)T * NN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  if ((rc = reduce_device(c, c->d_cube, c->d_cube, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, c->d_img))) {
+  if ((rc = reduce_device(c, c->d_cube, c->d_cube, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, c->d_img,
+                          host_in))) {
     cudaStreamSynchronize(c->stream);
     c->ev_used = 0;
     return rc;
