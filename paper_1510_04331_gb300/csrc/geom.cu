@@ -528,8 +528,11 @@ __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *
   __syncwarp();
 }
 
+// Register budget: 4 resident CTAs per SM for the row passes (measured
+// faster), 3 for the column passes, whose 8-byte strided accesses rely on
+// L1 reuse across the CTA's warps and lose it with more CTAs per SM.
 template <int KIND>
-__global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
+__global__ void __launch_bounds__(128, (KIND == SHIFT_Y || KIND == ROT_P2) ? 3 : 4) line_pass_w32(const LineArgs a) {
   constexpr int M = 1024, N = 512, PPC = 4;
   constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
   constexpr int NIN = (KIND == ROT_P3) ? M : N;
@@ -586,13 +589,29 @@ __global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
   }
 
   // ---- load: v[m] = element lane + 32 m of the line pair -----------------
+  // Column passes: the CTA's 8 adjacent columns are read row by row as
+  // 16-byte pieces (whole sectors) into the per-pair buffers first.
+  constexpr bool COLS = (KIND == SHIFT_Y || KIND == ROT_P2);
+  constexpr int RS = (KIND == ROT_P2) ? M : N;     // row stride of a column pass
+  const int col0 = 2 * PPC * blockIdx.x;           // first column of the CTA
+  if constexpr (COLS) {
+    for (int i = threadIdx.x; i < 2 * NIN; i += 32 * PPC) {
+      const int row = i >> 1, h = i & 1;
+      const float4 q4 = *reinterpret_cast<const float4 *>(fin + (size_t)row * RS + col0 + 4 * h);
+      sbuf[2 * h][pad32(row)] = make_float2(q4.x, q4.y);
+      sbuf[2 * h + 1][pad32(row)] = make_float2(q4.z, q4.w);
+    }
+    __syncthreads();
+  }
   float2 v[32];
 #pragma unroll
   for (int m = 0; m < 32; m++) {
     const int pos = lane + 32 * m;
     float2 z = make_float2(0.f, 0.f);
     if (32 * m < NIN) {
-      if constexpr (KIND == SHIFT_X) {
+      if constexpr (COLS) {
+        z = buf[pad32(pos)];
+      } else if constexpr (KIND == SHIFT_X) {
         z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
       } else if constexpr (KIND == SHIFT_Y) {
         z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
@@ -610,6 +629,7 @@ __global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
   if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
   }
+  if constexpr (COLS) __syncwarp();   // buf is the FFT's exchange buffer from here on
   fft1024_warp(v, lane, buf, tw);
 
   // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
@@ -659,6 +679,20 @@ __global__ void __launch_bounds__(128, 3) line_pass_w32(const LineArgs a) {
 
   // ---- inverse: the same stages on conj(V)/m; y = conj(result) ------------
   fft1024_warp(v, lane, buf, tw);
+  if constexpr (COLS) {
+    // through the per-pair buffers, then row by row as 16-byte pieces
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; r++)
+      if (32 * r < NOUT) buf[pad32(lane + 32 * r)] = make_float2(v[r].x, -v[r].y);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * NOUT; i += 32 * PPC) {
+      const int row = i >> 1, h = i & 1;
+      const float2 e0 = sbuf[2 * h][pad32(row)], e1 = sbuf[2 * h + 1][pad32(row)];
+      *reinterpret_cast<float4 *>(fout + (size_t)row * RS + col0 + 4 * h) = make_float4(e0.x, e0.y, e1.x, e1.y);
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 32; r++) {
     const int pos = lane + 32 * r;
