@@ -528,11 +528,10 @@ __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *
   __syncwarp();
 }
 
-// Register budget: 4 resident CTAs per SM for the row passes (measured
-// faster), 3 for the column passes, whose 8-byte strided accesses rely on
-// L1 reuse across the CTA's warps and lose it with more CTAs per SM.
+// Register budget for 4 resident CTAs per SM (measured faster than 3 for
+// every kind once the column passes move whole sectors; small spills).
 template <int KIND>
-__global__ void __launch_bounds__(128, (KIND == SHIFT_Y || KIND == ROT_P2) ? 3 : 4) line_pass_w32(const LineArgs a) {
+__global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
   constexpr int M = 1024, N = 512, PPC = 4;
   constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
   constexpr int NIN = (KIND == ROT_P3) ? M : N;
