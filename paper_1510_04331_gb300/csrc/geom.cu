@@ -420,8 +420,11 @@ __device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, i
 }
 
 // One CTA of a line pass: line pairs cx * LPC .. of frame blockIdx.y.
+// Register budget: 3 resident CTAs per SM for lines of up to 256 points, 2
+// for longer ones (measured: 3 is faster on the short lines, slower on the
+// 2048-point ones).
 template <int M, int KIND>
-__global__ void __launch_bounds__(256) line_pass_kernel(const LineArgs a) {
+__global__ void __launch_bounds__(256, (M <= 256) ? 3 : 2) line_pass_kernel(const LineArgs a) {
   extern __shared__ float2 smem[];
   __shared__ LineParam lp[2 * (4096 / M)];
   __shared__ int ident_s;
