@@ -605,13 +605,44 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
     }
     __syncthreads();
   }
+  // Rotation pass 1 with an odd number of quarter turns: the lines of
+  // rot90^q(frame) are columns of the frame, staged the same way.
+  //   q = 1: element pos >= 1 of lines col0 + j is frame[n - pos][col0 + j];
+  //   q = 3: element pos of line i >= 1 is frame[pos][n - i], i.e. columns
+  //          n - col0 - 7 .. n - col0 for the CTA's lines col0 .. col0 + 7.
+  const bool RCOLS = (KIND == ROT_P1) && (q & 1);
+  if (RCOLS) {
+    if (q == 1) {
+      for (int i = threadIdx.x; i < 2 * N; i += 32 * PPC) {
+        const int row = i >> 1, h = i & 1;
+        if (row == 0) continue;                        // would be element n
+        const float4 q4 = *reinterpret_cast<const float4 *>(fin + (size_t)row * N + col0 + 4 * h);
+        sbuf[2 * h][pad32(N - row)] = make_float2(q4.x, q4.y);
+        sbuf[2 * h + 1][pad32(N - row)] = make_float2(q4.z, q4.w);
+      }
+      if (threadIdx.x < PPC) sbuf[threadIdx.x][pad32(0)] = make_float2(0.f, 0.f);
+    } else {
+      const int cb = N - col0 - 8;                     // >= 0, multiple of 8
+      for (int pos = threadIdx.x; pos < N; pos += 32 * PPC) {
+        const float *rowp = fin + (size_t)pos * N;
+        const float4 lo4 = *reinterpret_cast<const float4 *>(rowp + cb);
+        const float4 hi4 = *reinterpret_cast<const float4 *>(rowp + cb + 4);
+        const float top = (col0 > 0) ? rowp[N - col0] : 0.f;   // line 0 of the frame is zero
+        sbuf[0][pad32(pos)] = make_float2(top, hi4.w);
+        sbuf[1][pad32(pos)] = make_float2(hi4.z, hi4.y);
+        sbuf[2][pad32(pos)] = make_float2(hi4.x, lo4.w);
+        sbuf[3][pad32(pos)] = make_float2(lo4.z, lo4.y);
+      }
+    }
+    __syncthreads();
+  }
   float2 v[32];
 #pragma unroll
   for (int m = 0; m < 32; m++) {
     const int pos = lane + 32 * m;
     float2 z = make_float2(0.f, 0.f);
     if (32 * m < NIN) {
-      if constexpr (COLS) {
+      if (COLS || RCOLS) {
         z = buf[pad32(pos)];
       } else if constexpr (KIND == SHIFT_X) {
         z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
@@ -631,7 +662,7 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
   if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
   }
-  if constexpr (COLS) __syncwarp();   // buf is the FFT's exchange buffer from here on
+  if (COLS || RCOLS) __syncwarp();   // buf is the FFT's exchange buffer from here on
   fft1024_warp(v, lane, buf, tw);
 
   // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
