@@ -48,6 +48,10 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Position of the (r+1)-th set bit of x (r = 0 for the lowest), r < popc(x):
@@ -140,68 +144,92 @@ __device__ __forceinline__ void hist_find(const uint32_t *hist, uint32_t krem, i
 // Median collapse
 // ---------------------------------------------------------------------------
 
+// One warp per pixel, COL_PPC pixels per CTA.  Keys in shared memory are
+// frame-major with an odd row stride (COL_KS words), so a warp reading its
+// pixel's keys of 32 consecutive frames hits 32 distinct banks.  Radix
+// select of the lower median: 8-bit digits, most significant first, digits
+// constant over the pixel's keys skipped, histograms by shared-memory
+// reductions.
+constexpr int COL_PPC = 4;
+constexpr int COL_KS = 5;
+
 template <bool SMEM>
-__global__ void __launch_bounds__(256) collapse_kernel(const CollapseArgs a) {
+__global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
-  uint32_t *hist_all = csm;                 // [8][256]
-  uint32_t *keys_all = csm + 8 * 256;       // [T][8] frame-major (SMEM only)
+  uint32_t *hist_all = csm;                       // [COL_PPC][256]
+  uint32_t *keys_all = csm + COL_PPC * 256;       // [T][COL_KS] (SMEM only)
   const long long T = a.T;
   const long long NN = (long long)a.n * a.n;
-  const long long p0 = (long long)blockIdx.x * 8;
+  const long long p0 = (long long)blockIdx.x * COL_PPC;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   bool bad = false;
   if constexpr (SMEM) {
-    float *stage = reinterpret_cast<float *>(keys_all);
-    for (long long j = threadIdx.x; j < 2 * T; j += 256)
-      cp_async16(stage + 4 * j, a.in + (j >> 1) * NN + p0 + 4 * (j & 1));
-    cp_async_wait_all();
-    __syncthreads();
-    for (long long j = threadIdx.x; j < 8 * T; j += 256) {
-      const float v = stage[j];
-      bad |= !isfinite(v);
-      keys_all[j] = f2key(v);
+    for (long long j = threadIdx.x; j < COL_PPC * T; j += 32 * COL_PPC) {
+      const long long t = j / COL_PPC;
+      const int q = (int)(j - t * COL_PPC);
+      cp_async4(keys_all + t * COL_KS + q, a.in + t * NN + p0 + q);
     }
-    if (bad) atomicOr(a.status, STATUS_NONFINITE);
+    cp_async_wait_all();
     __syncthreads();
   }
   uint32_t *hist = hist_all + w * 256;
   const long long p = p0 + w;
   auto key_at = [&](long long t) -> uint32_t {
-    if constexpr (SMEM) return keys_all[t * 8 + w];
+    if constexpr (SMEM) return keys_all[t * COL_KS + w];
     else return f2key(a.in[t * NN + p]);
   };
+  // keys in place (each warp converts its own pixel), finiteness, and the
+  // digits shared by every key
+  uint32_t orv = 0, andv = 0xffffffffu;
+  for (long long t = lane; t < T; t += 32) {
+    uint32_t key;
+    if constexpr (SMEM) {
+      const float v = __uint_as_float(keys_all[t * COL_KS + w]);
+      bad |= !isfinite(v);
+      key = f2key(v);
+      keys_all[t * COL_KS + w] = key;
+    } else {
+      const float v = a.in[t * NN + p];
+      bad |= !isfinite(v);
+      key = f2key(v);
+    }
+    orv |= key;
+    andv &= key;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    orv |= __shfl_xor_sync(FULL, orv, o);
+    andv &= __shfl_xor_sync(FULL, andv, o);
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
+  __syncwarp();
+  const uint32_t varying = orv ^ andv;
 
   const uint32_t k = (uint32_t)((T - 1) / 2);
-  uint32_t prefix = 0, pmask = 0, krem = k, cnt = 0;
+  uint32_t prefix = 0, pmask = 0, krem = k, cnt = (uint32_t)T;
   for (int pass = 0; pass < 4; pass++) {
     const int shift = 24 - 8 * pass;
+    if (((varying >> shift) & 255u) == 0) {   // every key has this digit
+      prefix |= andv & (0xffu << shift);
+      pmask |= 0xffu << shift;
+      continue;
+    }
 #pragma unroll
     for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0;
     __syncwarp();
-    for (long long base = 0; base < T; base += 32) {
-      const long long t = base + lane;
-      uint32_t tag = NOTAG;
-      if (t < T) {
-        const uint32_t key = key_at(t);
-        if constexpr (!SMEM) {
-          if (pass == 0) bad |= !isfinite(key2f(key));
-        }
-        if ((key & pmask) == prefix) tag = (key >> shift) & 255u;
-      }
-      const unsigned peers = __match_any_sync(FULL, tag);
-      if (tag != NOTAG && lane == __ffs(peers) - 1) hist[tag] += __popc(peers);
-      __syncwarp();
+#pragma unroll 4
+    for (long long t = lane; t < T; t += 32) {
+      const uint32_t key = key_at(t);
+      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
+    __syncwarp();
     uint32_t d, below;
     hist_find(hist, krem, lane, d, below, cnt);
     prefix |= d << shift;
     pmask |= 0xffu << shift;
     krem -= below;
     __syncwarp();
-  }
-  if constexpr (!SMEM) {
-    if (bad) atomicOr(a.status, STATUS_NONFINITE);
   }
   const float lo = key2f(prefix);
   float med = lo;
@@ -963,16 +991,16 @@ cudaError_t launch_adi_general(const AdiArgs &a, cudaStream_t st, int tcap);
 
 cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
   const long long NN = (long long)a.n * a.n;
-  const unsigned grid = (unsigned)(NN / 8);
-  if (a.T <= 4096) {
-    const size_t smem = (size_t)(8 * 256 + 8 * a.T) * sizeof(uint32_t);
+  const unsigned grid = (unsigned)(NN / COL_PPC);
+  if (a.T <= 8192) {
+    const size_t smem = (size_t)(COL_PPC * 256 + COL_KS * a.T) * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(collapse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    collapse_kernel<true><<<grid, 256, smem, st>>>(a);
+    collapse_kernel<true><<<grid, 32 * COL_PPC, smem, st>>>(a);
   } else {
-    const size_t smem = (size_t)(8 * 256) * sizeof(uint32_t);
-    collapse_kernel<false><<<grid, 256, smem, st>>>(a);
+    const size_t smem = (size_t)(COL_PPC * 256) * sizeof(uint32_t);
+    collapse_kernel<false><<<grid, 32 * COL_PPC, smem, st>>>(a);
   }
   return cudaGetLastError();
 }
