@@ -276,7 +276,10 @@ int graphic_get_precision(graphic_ctx *ctx, int32_t *precision);
 int graphic_profile(graphic_ctx *ctx, int enable);
 
 /* Copy the accumulated device milliseconds and launch counts of the first
- * n kernels (ids above) into ms[] and launches[] (host arrays of n). */
+ * n kernels (ids above) into ms[] and launches[] (host arrays of n).  The
+ * median PSF step is one bracketed interval of 1 to 3 kernel launches
+ * (general path, band paths); launches[] counts the kernels, and a grouped
+ * or persistent batch call (GRAPHIC_K_BATCH) counts as one graph launch. */
 int graphic_profile_read(graphic_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
 /* Name of kernel id `k` (static string), NULL if out of range. */

@@ -49,6 +49,7 @@ struct graphic_ctx {
   bool prof = false;
   double prof_ms[GRAPHIC_K_COUNT] = {};
   int64_t prof_n[GRAPHIC_K_COUNT] = {};
+  int64_t prof_extra[GRAPHIC_K_COUNT] = {};   // kernels beyond one per bracketed call
   std::vector<cudaEvent_t> ev;      // event pool, pairs
   std::vector<int> ev_kernel;       // kernel id per used pair
   size_t ev_used = 0;
@@ -162,6 +163,10 @@ void prof_end(graphic_ctx *c) {
   c->ev_used++;
 }
 void prof_collect(graphic_ctx *c) {
+  for (int k = 0; k < GRAPHIC_K_COUNT; k++) {
+    c->prof_n[k] += c->prof_extra[k];
+    c->prof_extra[k] = 0;
+  }
   for (size_t i = 0; i < c->ev_used; i++) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) {
@@ -480,8 +485,10 @@ int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t 
   a.n = n;
   a.n_ann = n_ann;
   prof_begin(c, GRAPHIC_K_ADI_MEDIAN);
-  cudaError_t e = launch_adi_median(a, c->stream);
+  int launched = 0;
+  cudaError_t e = launch_adi_median(a, c->stream, &launched);
   prof_end(c);
+  if (c->prof && launched > 1) c->prof_extra[GRAPHIC_K_ADI_MEDIAN] += launched - 1;
   if (e != cudaSuccess) return cuda_fail(e, "median PSF kernel");
   return GRAPHIC_OK;
 }
@@ -1420,6 +1427,7 @@ int graphic_profile(graphic_ctx *c, int enable) {
     for (int k = 0; k < GRAPHIC_K_COUNT; k++) {
       c->prof_ms[k] = 0;
       c->prof_n[k] = 0;
+      c->prof_extra[k] = 0;
     }
   }
   c->ev_used = 0;

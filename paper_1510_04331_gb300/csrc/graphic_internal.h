@@ -137,7 +137,9 @@ struct AdiArgs {
   int n_ann;             // A
   int wmax;              // largest W over the annuli (0: no band path)
 };
-cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st);
+// *launched (may be null) receives the number of kernels launched (1 to 3:
+// general path, band path W <= 16, band path W = 32).
+cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched = nullptr);
 
 struct CollapseArgs {
   const float *in;

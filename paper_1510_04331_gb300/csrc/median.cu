@@ -1005,12 +1005,16 @@ cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st) {
+cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched) {
+  int dummy = 0;
+  int &nl = launched ? *launched : dummy;
+  nl = 0;
   const long long NN = (long long)a.n * a.n;
   const int tcap = pow2_at_least(a.T, 32);
   // general kernel first: it reads every pixel of its groups and writes only
   // its own; the band launches then own disjoint 4-pixel groups
   cudaError_t e = launch_adi_general(a, st, tcap);
+  nl += (e == cudaSuccess);
   if (e != cudaSuccess || a.wmax == 0) return e;
   // band launches: groups whose widest bitmap is <= 16 words, then wider ones,
   // each with shared memory sized for its widest class
@@ -1022,6 +1026,7 @@ cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     adi_band_kernel<16><<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(b, tcap, 0);
     e = cudaGetLastError();
+    nl += (e == cudaSuccess);
     if (e != cudaSuccess) return e;
   }
   if (a.wmax > 16) {
@@ -1030,6 +1035,7 @@ cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     adi_band_kernel<32><<<(unsigned)(NN / BAND_PPC), 32 * BAND_PPC, L.total, st>>>(a, tcap, 16);
     e = cudaGetLastError();
+    nl += (e == cudaSuccess);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
