@@ -84,6 +84,17 @@ def job_throughput(units_per_rank_step, steps, world, max_ms):
     return units_per_rank_step * steps * world / (max_ms / 1e3)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a whole step of
+# one kernel, from ncu captures of the current kernels: (kernel, frames, n) ->
+# (bytes per step at that size, source).  Per launch = bytes / launches.
+MEASURED_TRAFFIC = {
+    ("adi_median", 2000, 512): (
+        3.641e9,
+        "ncu dram bytes of the median PSF launches (general + band) at 200 frames of the survey recipe "
+        "(364.1 MB), scaled x10 to 2000 frames (traffic grows with the frames)"),
+}
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -353,6 +364,10 @@ def run_gpu(args, rank, world, local_rank):
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
                 "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
                 "algorithmic_per_launch": amount}
+    mt = MEASURED_TRAFFIC.get((dom, T, n))
+    if mt:
+        roof["traffic"] = mt[0] / kd["launches_per_step"]
+        roof["traffic_source"] = mt[1]
     # whole-step HBM roofline (algorithmic 7 n^2 4 B per frame)
     alg_bytes = 7 * NN * 4 * T
     step_s = statistics.median(step_ms) / 1e3
