@@ -66,6 +66,8 @@ def _load():
             lib.oracle_alpha_min_deg.argtypes = [ctypes.c_double] * 3
             lib.oracle_alpha_min_deg.restype = ctypes.c_double
             lib.oracle_gate_mask.argtypes = [_d, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_double, _u8]
+            lib.oracle_gate_mask_t.argtypes = [_d, _d, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                               ctypes.c_double, _u8]
             lib.oracle_annulus_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _d, ctypes.c_int]
             lib.oracle_adi_subtract_pixels.argtypes = [
                 _d, ctypes.c_longlong, ctypes.c_int, _d, ctypes.c_double, ctypes.c_double, _d, ctypes.c_int,
@@ -79,6 +81,14 @@ def _load():
                                                               ctypes.c_longlong, _f]
             lib.oracle_reduce.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, _d, _d, ctypes.c_double,
                                           ctypes.c_double, _d, ctypes.c_int, _d]
+            lib.oracle_adi_subtract_pixels_t.argtypes = [
+                _d, ctypes.c_longlong, ctypes.c_int, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                _d, ctypes.c_int, _ll, ctypes.c_longlong, _d]
+            lib.oracle_adi_subtract_pixels_f32_t.argtypes = [
+                _f, ctypes.c_longlong, ctypes.c_int, _d, _d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                _d, ctypes.c_int, _ll, ctypes.c_longlong, _f]
+            lib.oracle_reduce_t.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, _d, _d, _d,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _d, ctypes.c_int, _d]
             lib.oracle_last_max_imag.restype = ctypes.c_double
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -164,10 +174,24 @@ def alpha_min_deg(fwhm: float, n_fwhm: float, r: float) -> float:
     return _load().oracle_alpha_min_deg(float(fwhm), float(n_fwhm), float(r))
 
 
-def gate_mask(parang, i: int, amin_deg: float) -> np.ndarray:
+def _times(times, T):
+    """Time stamps as a contiguous float64 array of T (None: no time gate)."""
+    if times is None:
+        return None
+    t = _c64(times)
+    if t.size != T:
+        raise ValueError("times must have one entry per frame")
+    return t
+
+
+def gate_mask(parang, i: int, amin_deg: float, times=None, t_max=None) -> np.ndarray:
+    """Reference set of frame i (Sect. 3.3); with ``times`` also |t_k - t_i| < t_max."""
     pa = _c64(parang)
     mask = np.zeros(pa.size, np.uint8)
-    _load().oracle_gate_mask(_p(pa, _d), pa.size, int(i), float(amin_deg), _p(mask, _u8))
+    tt = _times(times, pa.size)
+    _load().oracle_gate_mask_t(_p(pa, _d), None if tt is None else _p(tt, _d),
+                               float(t_max) if tt is not None else 0.0, pa.size, int(i), float(amin_deg),
+                               _p(mask, _u8))
     return mask.astype(bool)
 
 
@@ -176,12 +200,14 @@ def annulus_of(i: int, j: int, N: int, edges) -> int:
     return _load().oracle_annulus_of(int(i), int(j), int(N), _p(e, _d), e.size)
 
 
-def adi_subtract(cube: np.ndarray, parang, fwhm: float, n_fwhm: float, edges, pixels=None) -> np.ndarray:
+def adi_subtract(cube: np.ndarray, parang, fwhm: float, n_fwhm: float, edges, pixels=None, times=None,
+                 t_max=None) -> np.ndarray:
     """Angle-gated median PSF subtraction.
 
     FP64 for float64 cubes, FP32 median arithmetic for float32 cubes.  With
     ``pixels`` (flat indices) returns an array [n_pix][T]; without, the full
-    residual cube [T][N][N].
+    residual cube [T][N][N].  ``times`` / ``t_max``: the paper's maximum time
+    separation of reference frames (None: no time condition).
     """
     f32 = np.asarray(cube).dtype == np.float32
     c = np.ascontiguousarray(cube, dtype=np.float32 if f32 else np.float64)
@@ -192,12 +218,15 @@ def adi_subtract(cube: np.ndarray, parang, fwhm: float, n_fwhm: float, edges, pi
     pix = np.arange(N * N, dtype=np.int64) if full else np.ascontiguousarray(pixels, dtype=np.int64)
     out = np.empty((pix.size, T), np.float32 if f32 else np.float64)
     lib = _load()
+    tt = _times(times, T)
+    tp = None if tt is None else _p(tt, _d)
+    tm = float(t_max) if tt is not None else 0.0
     if f32:
-        rc = lib.oracle_adi_subtract_pixels_f32(_p(c, _f), T, N, _p(pa, _d), float(fwhm), float(n_fwhm),
-                                                _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _f))
+        rc = lib.oracle_adi_subtract_pixels_f32_t(_p(c, _f), T, N, _p(pa, _d), tp, tm, float(fwhm), float(n_fwhm),
+                                                  _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _f))
     else:
-        rc = lib.oracle_adi_subtract_pixels(_p(c, _d), T, N, _p(pa, _d), float(fwhm), float(n_fwhm),
-                                            _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _d))
+        rc = lib.oracle_adi_subtract_pixels_t(_p(c, _d), T, N, _p(pa, _d), tp, tm, float(fwhm), float(n_fwhm),
+                                              _p(e, _d), e.size, _p(pix, _ll), pix.size, _p(out, _d))
     if rc != 0:
         raise ValueError("bad arguments")
     if full:
@@ -221,8 +250,10 @@ def collapse_median(cube: np.ndarray, pixels=None) -> np.ndarray:
     return out.reshape(N, N) if full else out
 
 
-def reduce(cube: np.ndarray, dx, dy, parang, fwhm: float, n_fwhm: float, edges) -> np.ndarray:
-    """Shift, median PSF subtraction, derotation by -parang, median collapse."""
+def reduce(cube: np.ndarray, dx, dy, parang, fwhm: float, n_fwhm: float, edges, times=None,
+           t_max=None) -> np.ndarray:
+    """Shift, median PSF subtraction (optionally time-gated), derotation by
+    -parang, median collapse."""
     c = _c64(cube)
     T, N, _ = c.shape
     work = np.empty_like(c)
@@ -231,8 +262,10 @@ def reduce(cube: np.ndarray, dx, dy, parang, fwhm: float, n_fwhm: float, edges) 
     dy = _c64(np.broadcast_to(dy, (T,)))
     pa = _c64(parang)
     e = _c64(edges)
-    rc = _load().oracle_reduce(_p(c, _d), _p(work, _d), T, N, _p(dx, _d), _p(dy, _d), _p(pa, _d), float(fwhm),
-                               float(n_fwhm), _p(e, _d), e.size, _p(out, _d))
+    tt = _times(times, T)
+    rc = _load().oracle_reduce_t(_p(c, _d), _p(work, _d), T, N, _p(dx, _d), _p(dy, _d), _p(pa, _d),
+                                 None if tt is None else _p(tt, _d), float(t_max) if tt is not None else 0.0,
+                                 float(fwhm), float(n_fwhm), _p(e, _d), e.size, _p(out, _d))
     if rc != 0:
         raise ValueError("bad arguments")
     return out

@@ -14,9 +14,9 @@
  *     phasor, "at least double sized frames");
  *   - the three-shear Fourier rotation (Sect. 3.4, shear decomposition and
  *     the Fourier form of each shear, double sized frame);
- *   - the angle gate and the per-frame median PSF subtraction (Sect. 3.3,
- *     parallactic angle / reference-frame conditions, "without any
- *     combination coefficients");
+ *   - the angle gate, the optional maximum time separation t_max, and the
+ *     per-frame median PSF subtraction (Sect. 3.3, parallactic angle /
+ *     reference-frame conditions, "without any combination coefficients");
  *   - the final median collapse (Sect. 3.4, "merge all the frames").
  *
  * Conventions where the paper is silent or garbled (also listed in the
@@ -27,7 +27,8 @@
  * content counter-clockwise, (x,y) -> (x cos - y sin, x sin + y cos);
  * theta is split into 90q + theta', |theta'| <= 45, the 90q part is an
  * exact index map; alpha_min = 2 asin(n_fwhm FWHM / (2 r)); an empty
- * reference set falls back to the frame(s) farthest in angle; medians use
+ * reference set falls back to the frame(s) farthest in angle among those
+ * within t_max of the frame (all frames without a time gate); medians use
  * the IEEE total order, even counts average the two middle values.
  *
  * Threading: frames (geometric steps) and pixels (median steps) are spread
@@ -359,24 +360,37 @@ double oracle_alpha_min_deg(double fwhm, double n_fwhm, double r)
 }
 
 /* Exported: reference set of frame i for one alpha_min, as a 0/1 mask over
- * the T frames: |alpha_k - alpha_i| > alpha_min; when no frame qualifies,
- * the frame(s) with the largest |alpha_k - alpha_i|. */
-int oracle_gate_mask(const double *parang, long long T, long long i, double amin, unsigned char *mask)
+ * the T frames (Sect. 3.3): |t_k - t_i| < t_max and |alpha_k - alpha_i| >
+ * alpha_min.  times == NULL drops the time condition.  When no frame
+ * qualifies, the frame(s) with the largest |alpha_k - alpha_i| among those
+ * meeting the time condition. */
+int oracle_gate_mask_t(const double *parang, const double *times, double t_max, long long T, long long i,
+                       double amin, unsigned char *mask)
 {
     long long n = 0;
     for (long long k = 0; k < T; k++) {
-        mask[k] = fabs(parang[k] - parang[i]) > amin;
+        int in_time = times == NULL || fabs(times[k] - times[i]) < t_max;
+        mask[k] = in_time && fabs(parang[k] - parang[i]) > amin;
         n += mask[k];
     }
     if (n == 0) {
         double best = -1.0;
         for (long long k = 0; k < T; k++) {
+            if (times != NULL && !(fabs(times[k] - times[i]) < t_max)) continue;
             double dk = fabs(parang[k] - parang[i]);
             if (dk > best) best = dk;
         }
-        for (long long k = 0; k < T; k++) mask[k] = fabs(parang[k] - parang[i]) == best;
+        for (long long k = 0; k < T; k++) {
+            int in_time = times == NULL || fabs(times[k] - times[i]) < t_max;
+            mask[k] = in_time && fabs(parang[k] - parang[i]) == best;
+        }
     }
     return 0;
+}
+
+int oracle_gate_mask(const double *parang, long long T, long long i, double amin, unsigned char *mask)
+{
+    return oracle_gate_mask_t(parang, NULL, 0.0, T, i, amin, mask);
 }
 
 /* IEEE total-order keys: a larger key means a larger value, -0 < +0. */
@@ -439,9 +453,10 @@ int oracle_annulus_of(int i, int j, int N, const double *edges, int n_edges)
  * (flat indices p = i N + j), FP64.  out[n][t] = cube[t][p_n] - median of
  * cube[k][p_n] over the reference set of frame t; 0 for pixels outside the
  * annuli. */
-int oracle_adi_subtract_pixels(const double *cube, long long T, int N, const double *parang, double fwhm,
-                               double n_fwhm, const double *edges, int n_edges, const long long *pix,
-                               long long n_pix, double *out)
+int oracle_adi_subtract_pixels_t(const double *cube, long long T, int N, const double *parang,
+                                 const double *times, double t_max, double fwhm, double n_fwhm,
+                                 const double *edges, int n_edges, const long long *pix, long long n_pix,
+                                 double *out)
 {
     if (T < 1 || N < 2 || n_edges < 2) return -1;
     int A = n_edges - 1;
@@ -457,7 +472,7 @@ int oracle_adi_subtract_pixels(const double *cube, long long T, int N, const dou
         double *sel = (double *)malloc(sizeof(double) * (size_t)T);
         for (long long t = 0; t < T; t++) {
             if (a < 0) { out[n * T + t] = 0.0; continue; }
-            oracle_gate_mask(parang, T, t, amin[a], mask);
+            oracle_gate_mask_t(parang, times, t_max, T, t, amin[a], mask);
             long long m = 0;
             for (long long k = 0; k < T; k++)
                 if (mask[k]) sel[m++] = cube[(size_t)k * N * N + p];
@@ -470,11 +485,20 @@ int oracle_adi_subtract_pixels(const double *cube, long long T, int N, const dou
     return 0;
 }
 
+int oracle_adi_subtract_pixels(const double *cube, long long T, int N, const double *parang, double fwhm,
+                               double n_fwhm, const double *edges, int n_edges, const long long *pix,
+                               long long n_pix, double *out)
+{
+    return oracle_adi_subtract_pixels_t(cube, T, N, parang, NULL, 0.0, fwhm, n_fwhm, edges, n_edges, pix, n_pix,
+                                        out);
+}
+
 /* Exported: the same on FP32 data with FP32 median arithmetic and an FP32
  * subtraction (for the bit-exact comparison on identical inputs). */
-int oracle_adi_subtract_pixels_f32(const float *cube, long long T, int N, const double *parang, double fwhm,
-                                   double n_fwhm, const double *edges, int n_edges, const long long *pix,
-                                   long long n_pix, float *out)
+int oracle_adi_subtract_pixels_f32_t(const float *cube, long long T, int N, const double *parang,
+                                     const double *times, double t_max, double fwhm, double n_fwhm,
+                                     const double *edges, int n_edges, const long long *pix, long long n_pix,
+                                     float *out)
 {
     if (T < 1 || N < 2 || n_edges < 2) return -1;
     int A = n_edges - 1;
@@ -490,7 +514,7 @@ int oracle_adi_subtract_pixels_f32(const float *cube, long long T, int N, const 
         float *sel = (float *)malloc(sizeof(float) * (size_t)T);
         for (long long t = 0; t < T; t++) {
             if (a < 0) { out[n * T + t] = 0.0f; continue; }
-            oracle_gate_mask(parang, T, t, amin[a], mask);
+            oracle_gate_mask_t(parang, times, t_max, T, t, amin[a], mask);
             long long m = 0;
             for (long long k = 0; k < T; k++)
                 if (mask[k]) sel[m++] = cube[(size_t)k * N * N + p];
@@ -502,6 +526,14 @@ int oracle_adi_subtract_pixels_f32(const float *cube, long long T, int N, const 
     }
     free(amin);
     return 0;
+}
+
+int oracle_adi_subtract_pixels_f32(const float *cube, long long T, int N, const double *parang, double fwhm,
+                                   double n_fwhm, const double *edges, int n_edges, const long long *pix,
+                                   long long n_pix, float *out)
+{
+    return oracle_adi_subtract_pixels_f32_t(cube, T, N, parang, NULL, 0.0, fwhm, n_fwhm, edges, n_edges, pix,
+                                            n_pix, out);
 }
 
 /* Exported: median over the T frames for a list of pixels (FP64 / FP32). */
@@ -540,8 +572,9 @@ int oracle_collapse_median_pixels_f32(const float *cube, long long T, int N, con
 /* Exported: the whole reduction in FP64 -- shift by (dx, dy), median PSF
  * subtraction, derotation by theta = -parang, median collapse.  work must
  * hold T N N doubles; out holds N N. */
-int oracle_reduce(const double *cube, double *work, long long T, int N, const double *dx, const double *dy,
-                  const double *parang, double fwhm, double n_fwhm, const double *edges, int n_edges, double *out)
+int oracle_reduce_t(const double *cube, double *work, long long T, int N, const double *dx, const double *dy,
+                    const double *parang, const double *times, double t_max, double fwhm, double n_fwhm,
+                    const double *edges, int n_edges, double *out)
 {
     if (T < 1 || N < 2 || (N & 1) || n_edges < 2) return -1;
     size_t NN = (size_t)N * N;
@@ -551,7 +584,8 @@ int oracle_reduce(const double *cube, double *work, long long T, int N, const do
     double *theta = (double *)malloc(sizeof(double) * (size_t)T);
     oracle_shift(cube, work, T, N, dx, dy);
     for (size_t p = 0; p < NN; p++) pix[p] = (long long)p;
-    oracle_adi_subtract_pixels(work, T, N, parang, fwhm, n_fwhm, edges, n_edges, pix, (long long)NN, res);
+    oracle_adi_subtract_pixels_t(work, T, N, parang, times, t_max, fwhm, n_fwhm, edges, n_edges, pix,
+                                 (long long)NN, res);
     for (long long t = 0; t < T; t++)
         for (size_t p = 0; p < NN; p++) tmp[(size_t)t * NN + p] = res[p * (size_t)T + t];
     for (long long t = 0; t < T; t++) theta[t] = -parang[t];
@@ -562,4 +596,10 @@ int oracle_reduce(const double *cube, double *work, long long T, int N, const do
     free(res);
     free(theta);
     return 0;
+}
+
+int oracle_reduce(const double *cube, double *work, long long T, int N, const double *dx, const double *dy,
+                  const double *parang, double fwhm, double n_fwhm, const double *edges, int n_edges, double *out)
+{
+    return oracle_reduce_t(cube, work, T, N, dx, dy, parang, NULL, 0.0, fwhm, n_fwhm, edges, n_edges, out);
 }

@@ -370,3 +370,73 @@ def test_reduce_of_static_cube_is_zero():
     c = np.repeat(f, T, axis=0)
     out = oracle.reduce(c, np.zeros(T), np.zeros(T), np.linspace(0, 50, T), 4.0, 1.0, [0.0, 12.0])
     assert np.abs(out).max() <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# Time gate (maximum time separation t_max of the reference frames, Sect. 3.3)
+# --------------------------------------------------------------------------
+
+def _cube_1px(T, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((T, 4, 4))
+
+
+def test_time_gate_infinite_t_max_equals_no_time_gate():
+    T = 23
+    c = _cube_1px(T, 3)
+    pa = np.linspace(-30.0, 50.0, T)
+    times = np.arange(T) * 37.0
+    a = oracle.adi_subtract(c, pa, 1.0, 1.0, [0.0, 3.0])
+    b = oracle.adi_subtract(c, pa, 1.0, 1.0, [0.0, 3.0], times=times, t_max=np.inf)
+    assert np.array_equal(a, b)
+
+
+def test_time_gate_nearest_neighbours_closed_form():
+    # times = frame index, t_max = 1.5 and a vanishing alpha_min: the
+    # reference set of frame i is {i - 1, i + 1} (strict ">" removes frame i
+    # itself), so the residual is f_i minus the mean of its neighbours, and
+    # at the ends f_0 - f_1, f_{T-1} - f_{T-2}
+    T = 17
+    c = _cube_1px(T, 4)
+    pa = np.arange(T) * 2.0
+    res = oracle.adi_subtract(c, pa, 1e-9, 1e-9, [0.0, 3.0], times=np.arange(T, dtype=float), t_max=1.5)
+    ref = np.empty_like(c)
+    ref[1:-1] = c[1:-1] - 0.5 * (c[:-2] + c[2:])
+    ref[0] = c[0] - c[1]
+    ref[-1] = c[-1] - c[-2]
+    assert np.abs(res - ref).max() <= 1e-15
+
+
+def test_time_gate_empty_set_falls_back_to_farthest_frames_in_the_window():
+    # alpha_min = 180 deg (argument clamped): no frame qualifies, so the
+    # reference set is the frame(s) farthest in angle within |t_k - t_i| < 2.5,
+    # i.e. frames i - 2 and i + 2 (exact distances on an integer angle grid)
+    T = 15
+    c = _cube_1px(T, 5)
+    pa = np.arange(T) * 1.0
+    res = oracle.adi_subtract(c, pa, 1e6, 1.0, [0.0, 3.0], times=np.arange(T, dtype=float), t_max=2.5)
+    ref = np.empty_like(c)
+    for i in range(T):
+        nb = [k for k in (i - 2, i + 2) if 0 <= k < T]
+        if len(nb) == 1:                     # ends: window i..i+2 or i-2..i
+            ref[i] = c[i] - c[nb[0]]
+        else:
+            ref[i] = c[i] - 0.5 * (c[nb[0]] + c[nb[1]])
+    assert np.abs(res - ref).max() <= 1e-15
+
+
+def test_time_gate_shrinks_the_reference_set():
+    T = 40
+    pa = np.sort(np.random.default_rng(6).uniform(-60, 60, T))
+    times = np.cumsum(np.random.default_rng(7).uniform(0.5, 2.0, T))
+    amin = 5.0
+    for i in range(T):
+        full = oracle.gate_mask(pa, i, amin)
+        for tm in (3.0, 10.0, 1e9):
+            sub = oracle.gate_mask(pa, i, amin, times=times, t_max=tm)
+            inside = np.abs(times - times[i]) < tm
+            if (full & inside).any():
+                assert np.array_equal(sub, full & inside)
+            else:   # fallback: farthest in angle among the frames in time
+                d = np.where(inside, np.abs(pa - pa[i]), -1.0)
+                assert np.array_equal(sub, d == d.max())
