@@ -135,6 +135,26 @@ int graphic_reduce(graphic_ctx *ctx, const float *in, float *work, int64_t n_fra
                    const double *annuli_edges, int32_t n_edges, float *out);
 
 /*
+ * The same two calls with the paper's second reference-frame condition
+ * (Sect. 3.3, maximum time separation): frame k is in frame t's reference
+ * set only if also |times[k] - times[t]| < t_max, and the fallback for an
+ * empty set takes the frames farthest in angle among those within t_max.
+ * times: host array of n_frames (any unit, with t_max in the same unit);
+ * NULL means no time condition (then identical to the plain calls).  The
+ * times must be monotone along the order of the parallactic angles (as for
+ * a transit observed in time order), else GRAPHIC_ERR_UNSUPPORTED; t_max
+ * must be > 0 (GRAPHIC_ERR_INVALID_ARG).  With a time condition every pixel
+ * takes the general median path (sort + membership sweep), not the faster
+ * band path.
+ */
+int graphic_adi_subtract_ex(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n,
+                            const double *parang, const double *times, double t_max, double fwhm, double n_fwhm,
+                            const double *annuli_edges, int32_t n_edges);
+int graphic_reduce_ex(graphic_ctx *ctx, const float *in, float *work, int64_t n_frames, int32_t n,
+                      const double *dx, const double *dy, const double *parang, const double *times, double t_max,
+                      double fwhm, double n_fwhm, const double *annuli_edges, int32_t n_edges, float *out);
+
+/*
  * graphic_reduce with HOST buffers: copies host_in (n_frames*n*n floats) to
  * a device cube the context owns, reduces it, copies the n*n result back to
  * host_out.  Pinned (page-locked) host memory gives the fastest copies.

@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -404,14 +405,54 @@ static double alpha_min_deg(double fwhm, double n_fwhm, double r) {
   return 2.0 * asin(arg) * 180.0 / kPi;
 }
 
-void graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges,
-                       int32_t n_edges, AdiPlanHost &ap) {
+int graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges,
+                      int32_t n_edges, AdiPlanHost &ap, const double *times, double t_max) {
   const int A = n_edges - 1;
   ap.perm.resize(T);
   for (int64_t t = 0; t < T; t++) ap.perm[t] = (int)t;
   std::stable_sort(ap.perm.begin(), ap.perm.end(), [&](int x, int y) { return parang[x] < parang[y]; });
   ap.edge2.resize(n_edges);
   for (int i = 0; i < n_edges; i++) ap.edge2[i] = edges[i] * edges[i];
+  // time windows [A, B) in the angle order (the whole order without a time gate)
+  ap.ab.clear();
+  std::vector<int> wa(T, 0), wb(T, (int)T);
+  if (times) {
+    if (!(t_max > 0) || std::isnan(t_max)) return fail(GRAPHIC_ERR_INVALID_ARG, "t_max must be > 0");
+    std::vector<double> tt(T);
+    bool up = true, down = true;
+    for (int64_t s = 0; s < T; s++) {
+      tt[s] = times[ap.perm[s]];
+      if (!std::isfinite(tt[s])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite time stamp");
+      if (s) {
+        up &= tt[s] >= tt[s - 1];
+        down &= tt[s] <= tt[s - 1];
+      }
+    }
+    if (!up && !down)
+      return fail(GRAPHIC_ERR_UNSUPPORTED, "time stamps must be monotone in the order of the parallactic angles");
+    // |fl(t_k - t_s)| is monotone on either side of s: binary searches are exact
+    for (int64_t s = 0; s < T; s++) {
+      auto near = [&](int64_t k) { return fabs(tt[k] - tt[s]) < t_max; };
+      int64_t lo = 0, hi = s;   // [0, s]: false ... false true ... true
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (near(mid)) hi = mid; else lo = mid + 1;
+      }
+      wa[s] = (int)lo;
+      lo = s;
+      hi = T;                   // [s, T): true ... true false ... false
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (near(mid)) lo = mid + 1; else hi = mid;
+      }
+      wb[s] = (int)lo;
+    }
+    ap.ab.resize((size_t)T * 2);
+    for (int64_t s = 0; s < T; s++) {
+      ap.ab[2 * s] = wa[s];
+      ap.ab[2 * s + 1] = wb[s];
+    }
+  }
   ap.lr.assign((size_t)A * T * 2, 0);
   std::vector<double> al(T);
   for (int64_t s = 0; s < T; s++) al[s] = parang[ap.perm[s]];
@@ -436,16 +477,20 @@ void graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fw
         if (pred(mid)) hi = mid; else lo = mid + 1;
       }
       int64_t R = lo;
-      if (L == 0 && R == T) {
-        // empty: the frame(s) farthest in angle
-        const double best = std::max(fabs(al[0] - ai), fabs(al[T - 1] - ai));
-        int64_t l2 = 0;
-        while (l2 < T && fabs(al[l2] - ai) == best) l2++;
-        int64_t r2 = T;
-        if (l2 < T)
+      // clip the excluded range to the time window: the set is [W0, L) u [R, W1)
+      const int64_t W0 = wa[s], W1 = wb[s];
+      L = std::max(L, W0);
+      R = std::min(R, W1);
+      if (L == W0 && R == W1) {
+        // empty: the frame(s) of the window farthest in angle
+        const double best = std::max(fabs(al[W0] - ai), fabs(al[W1 - 1] - ai));
+        int64_t l2 = W0;
+        while (l2 < W1 && fabs(al[l2] - ai) == best) l2++;
+        int64_t r2 = W1;
+        if (l2 < W1)
           while (r2 > l2 && fabs(al[r2 - 1] - ai) == best) r2--;
         else
-          r2 = T;
+          r2 = W1;
         L = l2;
         R = r2;
       }
@@ -455,6 +500,7 @@ void graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fw
   }
   ap.band.assign((size_t)A * 4, 0);
   ap.wmax = 0;
+  if (times) return GRAPHIC_OK;   // general path only
   for (int a = 0; a < A; a++) {
     const int *lr = ap.lr.data() + (size_t)a * T * 2;
     plan_band(lr, T, ap.band.data() + 4 * a);
@@ -466,17 +512,20 @@ void graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fw
       }
     ap.wmax = std::max(ap.wmax, ap.band[4 * a + 2]);
   }
+  return GRAPHIC_OK;
 }
 
 namespace {
 
 int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
-                const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann) {
+                const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann,
+                const int *p_ab = nullptr) {
   AdiArgs a{};
   a.in = in;
   a.out = out;
   a.perm = p_perm;
   a.lr = p_lr;
+  a.ab = p_ab;
   a.edge2 = p_edge2;
   a.band = p_band;
   a.wmax = wmax;
@@ -517,7 +566,8 @@ const T *at(const graphic_ctx *c, size_t off) {
 // stream, each chunk's shift pass starting as soon as its copy is done.
 int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
-                  int32_t n_edges, float *out, const float *host_in = nullptr) {
+                  int32_t n_edges, float *out, const float *host_in = nullptr, const double *times = nullptr,
+                  double t_max = 0.0) {
   int rc = validate_shift(dx, dy, T, n);
   if (rc) return rc;
   rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges);
@@ -526,7 +576,7 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   rc = plan_rotate(parang, T, true, rp);
   if (rc) return rc;
   AdiPlanHost ap;
-  plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap);
+  if ((rc = plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap, times, t_max))) return rc;
   PlanBuilder pb;
   const size_t o_dx = pb.add(dx, T * sizeof(double));
   const size_t o_dy = pb.add(dy, T * sizeof(double));
@@ -537,6 +587,7 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
   const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
   const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
+  const size_t o_ab = pb.add(ap.ab.data(), ap.ab.size() * sizeof(int));
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
   if (!host_in) {
@@ -563,7 +614,7 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
     }
   }
   if ((rc = enqueue_adi(c, work, work, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
-                        at<int>(c, o_band), ap.wmax, n_edges - 1)))
+                        at<int>(c, o_band), ap.wmax, n_edges - 1, ap.ab.empty() ? nullptr : at<int>(c, o_ab))))
     return rc;
   if ((rc = enqueue_rotate(c, work, work, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q)))) return rc;
   if ((rc = enqueue_collapse(c, work, T, n, out))) return rc;
@@ -1247,26 +1298,33 @@ int graphic_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
   return end_call(c);
 }
 
-int graphic_adi_subtract(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *parang,
-                         double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+int graphic_adi_subtract_ex(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n,
+                            const double *parang, const double *times, double t_max, double fwhm, double n_fwhm,
+                            const double *edges, int32_t n_edges) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
   int rc = check_cube(in, out, T, n);
   if (rc) return rc;
   if ((rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges))) return rc;
   AdiPlanHost ap;
-  plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap);
+  if ((rc = plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap, times, t_max))) return rc;
   DeviceGuard g(c->device);
   PlanBuilder pb;
   const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
   const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
   const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
   const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
+  const size_t o_ab = pb.add(ap.ab.data(), ap.ab.size() * sizeof(int));
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
   if ((rc = enqueue_adi(c, in, out, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
-                        at<int>(c, o_band), ap.wmax, n_edges - 1)))
+                        at<int>(c, o_band), ap.wmax, n_edges - 1, ap.ab.empty() ? nullptr : at<int>(c, o_ab))))
     return rc;
   return end_call(c);
+}
+
+int graphic_adi_subtract(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *parang,
+                         double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+  return graphic_adi_subtract_ex(c, in, out, T, n, parang, nullptr, 0.0, fwhm, n_fwhm, edges, n_edges);
 }
 
 int graphic_collapse_median(graphic_ctx *c, const float *in, int64_t T, int32_t n, float *out) {
@@ -1280,20 +1338,27 @@ int graphic_collapse_median(graphic_ctx *c, const float *in, int64_t T, int32_t 
   return end_call(c);
 }
 
-int graphic_reduce(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
-                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
-                   int32_t n_edges, float *out) {
+int graphic_reduce_ex(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
+                      const double *dy, const double *parang, const double *times, double t_max, double fwhm,
+                      double n_fwhm, const double *edges, int32_t n_edges, float *out) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
   int rc = check_cube(in, work, T, n);
   if (rc) return rc;
   if (!out) return fail(GRAPHIC_ERR_INVALID_ARG, "null out");
   DeviceGuard g(c->device);
-  if ((rc = reduce_device(c, in, work, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, out))) {
+  if ((rc = reduce_device(c, in, work, T, n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges, out, nullptr, times,
+                          t_max))) {
     cudaStreamSynchronize(c->stream);
     c->ev_used = 0;
     return rc;
   }
   return end_call(c);
+}
+
+int graphic_reduce(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
+                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
+                   int32_t n_edges, float *out) {
+  return graphic_reduce_ex(c, in, work, T, n, dx, dy, parang, nullptr, 0.0, fwhm, n_fwhm, edges, n_edges, out);
 }
 
 int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t n, const double *dx,

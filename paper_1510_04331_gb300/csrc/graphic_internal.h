@@ -44,15 +44,23 @@ int validate_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, co
 // (stable), per annulus and sorted position s the set {k : |alpha_k -
 // alpha_s| > alpha_min(r_a)} as sorted-position ranges [0, L) u [R, T),
 // farthest frames when empty, and the rank band of each annulus' medians.
+// With time stamps (times != null) also |t_k - t_s| < t_max: the frames
+// within t_max form a window [A, B) of the angle order (times must be
+// monotone along it), the set is [A, L) u [R, B) with L, R clipped to the
+// window, the fallback takes the farthest frames within the window, and the
+// band path is off (its rank band assumes the whole frame set).
 struct AdiPlanHost {
   std::vector<int> perm;     // [T]
   std::vector<int> lr;       // [A][T][2]
+  std::vector<int> ab;       // [T][2] time windows (empty without a time gate)
   std::vector<double> edge2; // [A+1]
   std::vector<int> band;     // [A][4]
   int wmax = 0;
 };
-void plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
-              AdiPlanHost &ap);
+// Returns GRAPHIC_OK, or an error code (last error set) for times that are
+// not monotone in the angle order or a t_max that is not > 0.
+int plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
+             AdiPlanHost &ap, const double *times = nullptr, double t_max = 0.0);
 
 // Asynchronous context calls for the serving loop (capi.cu): a batch call on
 // the context's stream without the final synchronisation (the status word is
@@ -128,6 +136,8 @@ struct AdiArgs {
   float *out;
   const int *perm;       // [T] frame index at angle-sorted position s
   const int *lr;         // [A][T][2] (L, R) of the reference set of sorted frame s in annulus a
+  const int *ab;         // [T][2] time window (A, B) of sorted frame s, A <= L <= R <= B (null: [0, T));
+                         // the reference set is [A, L) u [R, B)
   const double *edge2;   // [A+1] squared annulus edges (FP64)
   const int *band;       // [A][4] (blo, bhi, W, 0): full-rank band holding every median the
                          // annulus needs, W = bitmap words per lane (0: general path)

@@ -409,40 +409,48 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   __syncwarp();
 
   // ---- 2. chunk-start membership bitmaps ---------------------------------
+  // Frame s (angle order) is in the set of query i when it lies in the time
+  // window [A_i, B_i) and outside the excluded range [L_i, R_i) (which lies
+  // inside the window): the XOR of two range indicators, so moving any of
+  // the four boundaries toggles exactly the frames it passes over.
   const int *LR = a.lr + (size_t)ann * T * 2;
+  const int2 *AB2 = reinterpret_cast<const int2 *>(a.ab);
+  auto window = [&](int i) -> int2 { return AB2 ? __ldg(&AB2[i]) : make_int2(0, T); };
   const int C = (T + 31) / 32;
   {
     const int L0 = __ldg(&LR[0]), R0 = __ldg(&LR[1]);
+    const int2 W0 = window(0);
     for (int wd = 0; wd < nw; wd++) {
       const int pos = wd * 32 + lane;
       bool mem = false;
       if (pos < T) {
         const int s = si[pos];
-        mem = (s < L0) || (s >= R0);
+        mem = (s >= W0.x && s < W0.y) && ((s < L0) || (s >= R0));
       }
       const unsigned word = __ballot_sync(FULL, mem);
       if (lane == 0) bm[wd * 32] = word;
     }
     __syncwarp();
-    int Lp = L0, Rp = R0;
+    int Lp = L0, Rp = R0, Ap = W0.x, Bp = W0.y;
     for (int c = 1; c < 32; c++) {
       const int i0 = c * C;
       if (i0 >= T) break;
       const int Lc = __ldg(&LR[2 * i0]), Rc = __ldg(&LR[2 * i0 + 1]);
+      const int2 Wc = window(i0);
       for (int wd = lane; wd < nw; wd += 32) bm[wd * 32 + c] = bm[wd * 32 + c - 1];
       __syncwarp();
-      const int a0 = min(Lp, Lc), a1 = max(Lp, Lc), b0 = min(Rp, Rc), b1 = max(Rp, Rc);
-      for (int s = a0 + lane; s < a1; s += 32) {
-        const int r = rk[s];
-        atomicXor(&bm[(r >> 5) * 32 + c], 1u << (r & 31));
-      }
-      for (int s = b0 + lane; s < b1; s += 32) {
-        const int r = rk[s];
-        atomicXor(&bm[(r >> 5) * 32 + c], 1u << (r & 31));
-      }
+      const int lo[4] = {min(Lp, Lc), min(Rp, Rc), min(Ap, Wc.x), min(Bp, Wc.y)};
+      const int hi[4] = {max(Lp, Lc), max(Rp, Rc), max(Ap, Wc.x), max(Bp, Wc.y)};
+      for (int q = 0; q < 4; q++)
+        for (int s = lo[q] + lane; s < hi[q]; s += 32) {
+          const int r = rk[s];
+          atomicXor(&bm[(r >> 5) * 32 + c], 1u << (r & 31));
+        }
       __syncwarp();
       Lp = Lc;
       Rp = Rc;
+      Ap = Wc.x;
+      Bp = Wc.y;
     }
   }
 
@@ -453,7 +461,8 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   bool fail = false;
   if (i0 < T) {
     int L = __ldg(&LR[2 * i0]), R = __ldg(&LR[2 * i0 + 1]);
-    int nset = L + (T - R);
+    int2 W = window(i0);
+    int nset = (W.y - W.x) - (R - L);
     int k = (nset - 1) >> 1;
     int pos = -1, acc = 0;
     for (int wd = 0; wd < nw; wd++) {
@@ -471,11 +480,13 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
     int2 nxt = __ldg(&LR2[i0]);
     for (int i = i0; i < i1 && !fail; i++) {
       const int Ln = nxt.x, Rn = nxt.y;
+      const int2 Wn = window(i);
       if (i + 1 < i1) nxt = __ldg(&LR2[i + 1]);
       // toggle frames whose membership changes; keep `below` = set bits < pos
-      for (int pass = 0; pass < 2; pass++) {
-        const int s0 = pass == 0 ? min(L, Ln) : min(R, Rn);
-        const int s1 = pass == 0 ? max(L, Ln) : max(R, Rn);
+      const int npass = AB2 ? 4 : 2;
+      for (int pass = 0; pass < npass; pass++) {
+        const int s0 = pass == 0 ? min(L, Ln) : pass == 1 ? min(R, Rn) : pass == 2 ? min(W.x, Wn.x) : min(W.y, Wn.y);
+        const int s1 = pass == 0 ? max(L, Ln) : pass == 1 ? max(R, Rn) : pass == 2 ? max(W.x, Wn.x) : max(W.y, Wn.y);
         for (int s = s0; s < s1; s++) {
           const int r = rk[s];
           uint32_t *wp = &bm[(r >> 5) * 32 + c];
@@ -487,7 +498,8 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
       }
       L = Ln;
       R = Rn;
-      nset = L + (T - R);
+      W = Wn;
+      nset = (W.y - W.x) - (R - L);
       k = (nset - 1) >> 1;
       // walk the pointer to the k-th set bit
       for (int guard = 0; guard < 4 * 2048 + 8; guard++) {

@@ -567,7 +567,10 @@ int graphic_server_submit(graphic_server *s, const graphic_request *rq, int64_t 
   r->dy.assign(rq->dy, rq->dy + T);
   r->theta.resize(T);
   for (int64_t t = 0; t < T; t++) r->theta[t] = -rq->parang[t];
-  graphic::plan_adi(rq->parang, T, rq->fwhm, rq->n_fwhm, rq->edges, rq->n_edges, r->ap);
+  if ((rc = graphic::plan_adi(rq->parang, T, rq->fwhm, rq->n_fwhm, rq->edges, rq->n_edges, r->ap))) {
+    delete r;
+    return rc;
+  }
   r->n_ann = rq->n_edges - 1;
   const size_t NN = (size_t)r->n * r->n;
   r->cube_bytes = (size_t)T * NN * sizeof(float);

@@ -111,6 +111,10 @@ _SIGS = {
     "graphic_adi_subtract": [_P, _P, _P, _I64, _I32, _D, ctypes.c_double, ctypes.c_double, _D, _I32],
     "graphic_collapse_median": [_P, _P, _I64, _I32, _P],
     "graphic_reduce": [_P, _P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
+    "graphic_adi_subtract_ex": [_P, _P, _P, _I64, _I32, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                _D, _I32],
+    "graphic_reduce_ex": [_P, _P, _P, _I64, _I32, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double, _D, _I32, _P],
     "graphic_reduce_host": [_P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
     "graphic_profile": [_P, ctypes.c_int],
     "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
@@ -218,16 +222,20 @@ class Context:
         _check(lib().graphic_rotate(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, pth))
         return out
 
-    def graphic_adi_subtract(self, cube, parang, fwhm, n_fwhm, edges, out=None):
+    def graphic_adi_subtract(self, cube, parang, fwhm, n_fwhm, edges, out=None, times=None, t_max=None):
+        """Median PSF subtraction; ``times`` / ``t_max`` add the maximum time
+        separation of the reference frames (graphic_adi_subtract_ex)."""
         import torch
         cube = _cube(cube)
         T, n = cube.shape[0], cube.shape[1]
         out = torch.empty_like(cube) if out is None else _cube(out, "out")
         paa, ppa = _f64(parang, T)
+        ta, pta = (None, None) if times is None else _f64(times, T)
         ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
         self._stream()
-        _check(lib().graphic_adi_subtract(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, ppa,
-                                          float(fwhm), float(n_fwhm), ea.ctypes.data_as(_D), ea.size))
+        _check(lib().graphic_adi_subtract_ex(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, ppa, pta,
+                                             float(t_max) if times is not None else 0.0, float(fwhm),
+                                             float(n_fwhm), ea.ctypes.data_as(_D), ea.size))
         return out
 
     def graphic_collapse_median(self, cube, out=None):
@@ -239,7 +247,9 @@ class Context:
         _check(lib().graphic_collapse_median(self.h, _P(cube.data_ptr()), T, n, _P(out.data_ptr())))
         return out
 
-    def graphic_reduce(self, cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None):
+    def graphic_reduce(self, cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None, times=None,
+                       t_max=None):
+        """Full reduction; ``times`` / ``t_max`` as in graphic_adi_subtract."""
         import torch
         cube = _cube(cube)
         T, n = cube.shape[0], cube.shape[1]
@@ -248,11 +258,12 @@ class Context:
         dxa, pdx = _f64(dx, T)
         dya, pdy = _f64(dy, T)
         paa, ppa = _f64(parang, T)
+        ta, pta = (None, None) if times is None else _f64(times, T)
         ea = np.ascontiguousarray(np.asarray(edges, np.float64).ravel())
         self._stream()
-        _check(lib().graphic_reduce(self.h, _P(cube.data_ptr()), _P(work.data_ptr()), T, n, pdx, pdy, ppa,
-                                    float(fwhm), float(n_fwhm), ea.ctypes.data_as(_D), ea.size,
-                                    _P(out.data_ptr())))
+        _check(lib().graphic_reduce_ex(self.h, _P(cube.data_ptr()), _P(work.data_ptr()), T, n, pdx, pdy, ppa, pta,
+                                       float(t_max) if times is not None else 0.0, float(fwhm), float(n_fwhm),
+                                       ea.ctypes.data_as(_D), ea.size, _P(out.data_ptr())))
         return out
 
     def graphic_reduce_host(self, cube_host, dx, dy, parang, fwhm, n_fwhm, edges, out_host=None):
@@ -463,16 +474,17 @@ def graphic_rotate(cube, theta_deg, out=None):
     return context(cube.device.index).graphic_rotate(cube, theta_deg, out)
 
 
-def graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out=None):
-    return context(cube.device.index).graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out)
+def graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out=None, times=None, t_max=None):
+    return context(cube.device.index).graphic_adi_subtract(cube, parang, fwhm, n_fwhm, edges, out, times, t_max)
 
 
 def graphic_collapse_median(cube, out=None):
     return context(cube.device.index).graphic_collapse_median(cube, out)
 
 
-def graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None):
-    return context(cube.device.index).graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work, out)
+def graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work=None, out=None, times=None, t_max=None):
+    return context(cube.device.index).graphic_reduce(cube, dx, dy, parang, fwhm, n_fwhm, edges, work, out, times,
+                                                     t_max)
 
 
 def graphic_rotate_noalloc(cube, theta_deg, out):
