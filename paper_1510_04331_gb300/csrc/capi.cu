@@ -11,7 +11,8 @@
 //           > alpha_min} (Sect. 3.3) written as sorted-position ranges
 //           [0, L) u [R, T) -- exact, because |fl(alpha_k - alpha_s)| is
 //           monotone on either side of s -- with the farthest-frame fallback
-//           when that set is empty.
+//           when that set is empty; with time stamps also the window [A, B)
+//           of frames within t_max (Sect. 3.3), the set then [A, L) u [R, B).
 // Work order of graphic_rotate / graphic_shift: frames are processed in
 // chunks sized so that a chunk's intermediate data (the n x 2n scratch of
 // the rotation) stays within the L2 cache between the passes.
