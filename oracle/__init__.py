@@ -89,6 +89,11 @@ def _load():
                 _d, ctypes.c_int, _ll, ctypes.c_longlong, _f]
             lib.oracle_reduce_t.argtypes = [_d, _d, ctypes.c_longlong, ctypes.c_int, _d, _d, _d, _d,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _d, ctypes.c_int, _d]
+            lib.oracle_sky_median_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, _d, _d, ctypes.c_double, _f]
+            lib.oracle_sky_subtract_f32.argtypes = [_f, _f, ctypes.c_longlong, ctypes.c_int, _f, ctypes.c_int, _d,
+                                                    _d]
+            lib.oracle_bad_pixel_map_f32.argtypes = [_f, ctypes.c_int, ctypes.c_double, _u8]
+            lib.oracle_bad_pixel_fix_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, _u8]
             lib.oracle_last_max_imag.restype = ctypes.c_double
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -269,3 +274,60 @@ def reduce(cube: np.ndarray, dx, dy, parang, fwhm: float, n_fwhm: float, edges, 
     if rc != 0:
         raise ValueError("bad arguments")
     return out
+
+
+# --------------------------------------------------------------------------
+# Image-quality pre-processing (Sect. 3.2), FP32 data
+# --------------------------------------------------------------------------
+
+def _f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def sky_median(cube, mask_x=None, mask_y=None, mask_r=0.0) -> np.ndarray:
+    """Master sky: per-pixel median over the frames of the finite values
+    outside each frame's star mask (NaN where none is left)."""
+    c = _f32(cube)
+    T, N, _ = c.shape
+    sky = np.empty((N, N), np.float32)
+    mx = None if mask_x is None else _c64(np.broadcast_to(mask_x, (T,)))
+    my = None if mask_y is None else _c64(np.broadcast_to(mask_y, (T,)))
+    rc = _load().oracle_sky_median_f32(_p(c, _f), T, N, None if mx is None else _p(mx, _d),
+                                       None if my is None else _p(my, _d), float(mask_r), _p(sky, _f))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return sky
+
+
+def sky_subtract(cube, skies, frame_times, sky_times) -> np.ndarray:
+    """Each frame minus the master sky closest in time (earlier on a tie)."""
+    c = _f32(cube)
+    T, N, _ = c.shape
+    sk = _f32(skies)
+    ft = _c64(frame_times)
+    st = _c64(sky_times)
+    out = np.empty_like(c)
+    rc = _load().oracle_sky_subtract_f32(_p(c, _f), _p(out, _f), T, N, _p(sk, _f), sk.shape[0], _p(ft, _d),
+                                         _p(st, _d))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+def bad_pixel_map(ref, C: float) -> np.ndarray:
+    """Pixels of ref farther than C sigma from its median (bool map)."""
+    r = _f32(ref)
+    N = r.shape[0]
+    m = np.zeros((N, N), np.uint8)
+    _load().oracle_bad_pixel_map_f32(_p(r, _f), N, float(C), _p(m, _u8))
+    return m.astype(bool)
+
+
+def bad_pixel_fix(cube, bad_map=None):
+    """Flagged and non-finite pixels replaced by the median of their finite
+    8-neighbours, pass by pass until none is left.  Returns (cube, status)."""
+    c = np.array(cube, dtype=np.float32, copy=True, order="C")
+    T, N, _ = c.shape
+    m = None if bad_map is None else np.ascontiguousarray(bad_map, dtype=np.uint8)
+    st = _load().oracle_bad_pixel_fix_f32(_p(c, _f), T, N, None if m is None else _p(m, _u8))
+    return c, st

@@ -603,3 +603,130 @@ int oracle_reduce(const double *cube, double *work, long long T, int N, const do
 {
     return oracle_reduce_t(cube, work, T, N, dx, dy, parang, NULL, 0.0, fwhm, n_fwhm, edges, n_edges, out);
 }
+
+/* ---------------------------------------------------------------------- */
+/* Image-quality pre-processing (Sect. 3.2)                               */
+/* ---------------------------------------------------------------------- */
+
+/* Exported: master sky (Sect. 3.2, "Master sky"): per pixel the median over
+ * the T frames of the values that are finite and lie outside the star mask
+ * of their frame (distance to (mask_x[t], mask_y[t]) below mask_r, pixel
+ * coordinates x = column, y = row; mask_x == NULL: no mask).  A pixel with
+ * no such value gets NaN.  FP32 data, FP32 median rule (the two middle
+ * values averaged for even counts). */
+int oracle_sky_median_f32(const float *cube, long long T, int N, const double *mask_x, const double *mask_y,
+                          double mask_r, float *sky)
+{
+    if (T < 1 || N < 1) return -1;
+    size_t NN = (size_t)N * N;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (long long p = 0; p < (long long)NN; p++) {
+        float *v = (float *)malloc(sizeof(float) * (size_t)T);
+        long long m = 0;
+        double x = (double)(p % N), y = (double)(p / N);
+        for (long long t = 0; t < T; t++) {
+            float f = cube[(size_t)t * NN + p];
+            if (!isfinite(f)) continue;
+            if (mask_x) {
+                double ddx = x - mask_x[t], ddy = y - mask_y[t];
+                if (ddx * ddx + ddy * ddy < mask_r * mask_r) continue;
+            }
+            v[m++] = f;
+        }
+        sky[p] = m ? median32(v, m) : NAN;
+        free(v);
+    }
+    return 0;
+}
+
+/* Exported: sky subtraction (Sect. 3.2): out[t] = in[t] - skies[j], j the
+ * master sky closest in time to frame t (the earlier one on a tie). */
+int oracle_sky_subtract_f32(const float *cube, float *out, long long T, int N, const float *skies, int n_skies,
+                            const double *frame_times, const double *sky_times)
+{
+    if (T < 0 || n_skies < 1) return -1;
+    size_t NN = (size_t)N * N;
+    for (long long t = 0; t < T; t++) {
+        int j = 0;
+        for (int s = 1; s < n_skies; s++)
+            if (fabs(sky_times[s] - frame_times[t]) < fabs(sky_times[j] - frame_times[t])) j = s;
+        for (size_t p = 0; p < NN; p++) out[(size_t)t * NN + p] = cube[(size_t)t * NN + p] - skies[(size_t)j * NN + p];
+    }
+    return 0;
+}
+
+/* Exported: bad pixel map (Sect. 3.2, "Bad pixel correction"): map[p] = 1
+ * when |ref[p] - median(ref)| > C sigma, sigma the population standard
+ * deviation of ref (FP64), the median of the N x N values in FP32 (two
+ * middle values averaged for an even count), the comparison in FP64. */
+int oracle_bad_pixel_map_f32(const float *ref, int N, double C, unsigned char *map)
+{
+    size_t NN = (size_t)N * N;
+    if (NN < 1) return -1;
+    float *v = (float *)malloc(sizeof(float) * NN);
+    double mean = 0.0;
+    for (size_t p = 0; p < NN; p++) {
+        v[p] = ref[p];
+        mean += ref[p];
+    }
+    mean /= (double)NN;
+    double ss = 0.0;
+    for (size_t p = 0; p < NN; p++) ss += ((double)ref[p] - mean) * ((double)ref[p] - mean);
+    double sigma = sqrt(ss / (double)NN);
+    float med = median32(v, (long long)NN);
+    for (size_t p = 0; p < NN; p++) map[p] = fabs((double)ref[p] - (double)med) > C * sigma;
+    free(v);
+    return 0;
+}
+
+/* Exported: bad pixel correction (Sect. 3.2): in every frame the flagged
+ * pixels (map != NULL) and the non-finite ones become NaN, then each NaN
+ * pixel with at least one finite 8-neighbour takes the median of those
+ * neighbours (FP32 median rule), all pixels of a pass reading the previous
+ * pass's values, until no NaN is left (clumps fill from their border
+ * inwards).  Returns 0, or 1 when a frame has no finite pixel at all. */
+int oracle_bad_pixel_fix_f32(float *cube, long long T, int N, const unsigned char *map)
+{
+    size_t NN = (size_t)N * N;
+    int status = 0;
+    for (long long t = 0; t < T; t++) {
+        float *f = cube + (size_t)t * NN;
+        float *g = (float *)malloc(sizeof(float) * NN);
+        long long nan_left = 0;
+        for (size_t p = 0; p < NN; p++) {
+            if ((map && map[p]) || !isfinite(f[p])) f[p] = NAN;
+            nan_left += isnan(f[p]) ? 1 : 0;
+        }
+        while (nan_left > 0) {
+            long long fixed = 0;
+            memcpy(g, f, sizeof(float) * NN);
+            for (int i = 0; i < N; i++)
+                for (int j = 0; j < N; j++) {
+                    if (!isnan(g[(size_t)i * N + j])) continue;
+                    float nb[8];
+                    long long m = 0;
+                    for (int di = -1; di <= 1; di++)
+                        for (int dj = -1; dj <= 1; dj++) {
+                            if (!di && !dj) continue;
+                            int ii = i + di, jj = j + dj;
+                            if (ii < 0 || ii >= N || jj < 0 || jj >= N) continue;
+                            float w = g[(size_t)ii * N + jj];
+                            if (!isnan(w)) nb[m++] = w;
+                        }
+                    if (m) {
+                        f[(size_t)i * N + j] = median32(nb, m);
+                        fixed++;
+                    }
+                }
+            if (fixed == 0) {
+                status = 1;
+                break;
+            }
+            nan_left -= fixed;
+        }
+        free(g);
+    }
+    return status;
+}

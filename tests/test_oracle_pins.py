@@ -440,3 +440,100 @@ def test_time_gate_shrinks_the_reference_set():
             else:   # fallback: farthest in angle among the frames in time
                 d = np.where(inside, np.abs(pa - pa[i]), -1.0)
                 assert np.array_equal(sub, d == d.max())
+
+
+# --------------------------------------------------------------------------
+# Image-quality pre-processing (Sect. 3.2): master sky, bad pixels
+# --------------------------------------------------------------------------
+
+def test_sky_median_equals_numpy_nanmedian_with_mask():
+    rng = np.random.default_rng(11)
+    T, N = 9, 20
+    c = rng.normal(100.0, 5.0, (T, N, N)).astype(np.float32)
+    c[2, 3, 4] = np.nan
+    c[:, 7, 7] = np.nan                                  # no value left: NaN
+    mx, my, r = rng.uniform(5, 15, T), rng.uniform(5, 15, T), 3.0
+    ref = c.copy()
+    yy, xx = np.mgrid[0:N, 0:N]
+    for t in range(T):
+        ref[t][(xx - mx[t]) ** 2 + (yy - my[t]) ** 2 < r * r] = np.nan
+    with np.errstate(all="ignore"):
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            want = np.nanmedian(ref, axis=0).astype(np.float32)
+    got = oracle.sky_median(c, mx, my, r)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.array_equal(got[ok], want[ok])
+
+
+def test_sky_median_of_identical_frames_is_the_frame():
+    f = np.random.default_rng(12).normal(0, 1, (1, 16, 16)).astype(np.float32)
+    assert np.array_equal(oracle.sky_median(np.repeat(f, 6, axis=0)), f[0])
+
+
+def test_sky_subtract_uses_the_closest_sky_in_time():
+    rng = np.random.default_rng(13)
+    T, N = 7, 8
+    c = rng.normal(0, 1, (T, N, N)).astype(np.float32)
+    skies = rng.normal(0, 1, (3, N, N)).astype(np.float32)
+    ft = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0])
+    st = np.array([0.5, 3.0, 5.5])
+    # frame 0 -> sky 0 (0.5), 1 -> tie 0.5 vs 2.0: sky 0, 2 -> sky 1, 3 -> 1, 4 -> 1 (1.0 vs 1.5), 5 -> 2, 6 -> 2
+    j = [0, 0, 1, 1, 1, 2, 2]
+    want = np.stack([c[t] - skies[j[t]] for t in range(T)])
+    assert np.array_equal(oracle.sky_subtract(c, skies, ft, st), want)
+
+
+def test_bad_pixel_map_flags_planted_outliers():
+    rng = np.random.default_rng(14)
+    N = 32
+    ref = rng.normal(10.0, 1.0, (N, N)).astype(np.float32)
+    hot = [(3, 4), (20, 7), (31, 31)]
+    for (i, j) in hot:
+        ref[i, j] = 500.0
+    ref[10, 10] = -400.0
+    m = oracle.bad_pixel_map(ref, 5.0)
+    med = np.median(ref)
+    sig = ref.astype(np.float64).std()
+    assert np.array_equal(m, np.abs(ref.astype(np.float64) - float(med)) > 5.0 * sig)
+    assert m.sum() == 4 and m[10, 10] and all(m[i, j] for (i, j) in hot)
+
+
+def test_bad_pixel_fix_single_pixel_and_clump():
+    N = 9
+    f = (np.arange(N * N, dtype=np.float32).reshape(1, N, N) * 1.5) ** 1.1
+    bad = np.zeros((N, N), bool)
+    bad[1, 1] = True                                      # isolated: median of its 8 neighbours
+    bad[4:7, 4:7] = True                                  # 3 x 3 clump: border first, centre next
+    got, st = oracle.bad_pixel_fix(f, bad)
+    assert st == 0
+    g = f[0].copy()
+    nb = [g[i, j] for i in range(0, 3) for j in range(0, 3) if (i, j) != (1, 1)]
+    assert got[0, 1, 1] == np.median(np.array(nb, np.float32))
+    # the clump, pass by pass, written out here independently
+    h = g.copy()
+    h[1, 1] = np.nan
+    h[4:7, 4:7] = np.nan
+    while np.isnan(h).any():
+        prev = h.copy()
+        for i in range(N):
+            for j in range(N):
+                if not np.isnan(prev[i, j]):
+                    continue
+                vals = [prev[a, b] for a in range(max(0, i - 1), min(N, i + 2))
+                        for b in range(max(0, j - 1), min(N, j + 2)) if (a, b) != (i, j) and not np.isnan(prev[a, b])]
+                if vals:
+                    h[i, j] = np.median(np.array(vals, np.float32))
+    assert np.array_equal(got[0], h)
+
+
+def test_bad_pixel_fix_constant_frame_and_hopeless_frame():
+    f = np.full((2, 6, 6), 3.25, np.float32)
+    f[0, 0, 0] = np.inf
+    f[0, 2:5, 2:5] = np.nan
+    f[1] = np.nan
+    got, st = oracle.bad_pixel_fix(f)
+    assert np.array_equal(got[0], np.full((6, 6), 3.25, np.float32))
+    assert st == 1                                        # frame 1 has no finite pixel
