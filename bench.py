@@ -530,6 +530,87 @@ def run_precision(args, rank, world, local_rank):
 
 
 # ---------------------------------------------------------------------------
+# image-quality pre-processing (Sect. 3.2) of the survey-sized cube
+# ---------------------------------------------------------------------------
+
+def run_prep(args, rank, world, local_rank):
+    """Each step: 20 master skies (each the masked median of 50 dithered sky
+    frames), the subtraction of the nearest sky from 2000 science frames of
+    512 x 512, the bad pixel map of a master dark (C = 5) and the
+    neighbour-median correction of the 2000 frames (0.1 % hot pixels and
+    3 x 3 clumps, plus NaN from the masks)."""
+    import torch
+    from paper_1510_04331_gb300 import graphic
+
+    torch.cuda.set_device(local_rank)
+    T, n, ns, nsf = (args.frames or 2000), 512, 20, 50
+    gen = torch.Generator(device="cuda").manual_seed(5 + rank)
+    sci = torch.randn((T, n, n), generator=gen, device="cuda") * 10.0 + 100.0
+    skyf = torch.randn((nsf, n, n), generator=gen, device="cuda") * 3.0 + 100.0
+    dark = torch.randn((n, n), generator=gen, device="cuda")
+    rng = np.random.default_rng(5)
+    hot = rng.choice(n * n, n * n // 1000, replace=False)
+    dark.view(-1)[torch.from_numpy(hot).cuda()] = 100.0
+    for (r0, c0) in rng.integers(10, n - 10, (5, 2)):
+        dark[r0:r0 + 3, c0:c0 + 3] = 100.0
+    mx, my = rng.uniform(100, 400, nsf), rng.uniform(100, 400, nsf)
+    frame_t = np.linspace(0.0, 1.0, T)
+    sky_t = np.linspace(0.0, 1.0, ns)
+    ctx = graphic.Context(local_rank)
+    skies = torch.empty((ns, n, n), device="cuda")
+    out = torch.empty_like(sci)
+
+    def step(ev=None):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if ev is not None else None
+        if marks:
+            marks[0].record()
+        for j in range(ns):
+            ctx.graphic_sky_median(skyf, mx, my, 30.0, out=skies[j])
+        if marks:
+            marks[1].record()
+        ctx.graphic_sky_subtract(sci, skies, frame_t, sky_t, out=out)
+        if marks:
+            marks[2].record()
+        m = ctx.graphic_bad_pixel_map(dark, 5.0)
+        if marks:
+            marks[3].record()
+        ctx.graphic_bad_pixel_fix(out, m)
+        if marks:
+            marks[4].record()
+            ev.append(marks)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        step(evs)
+    torch.cuda.synchronize()
+    names = ["sky_median_x20", "sky_subtract", "bad_pixel_map", "bad_pixel_fix"]
+    per = {k: statistics.median(e[i].elapsed_time(e[i + 1]) for e in evs) for i, k in enumerate(names)}
+    tot = statistics.median(e[0].elapsed_time(e[4]) for e in evs)
+    hbm, _ = peaks()
+    sub_bytes = 2 * T * n * n * 4
+    line = {
+        "metric": "frames/s, image-quality pre-processing (master skies, sky subtraction, bad pixels)",
+        "value": T / (tot / 1e3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{T} science frames of {n}x{n}, {ns} master skies of {nsf} masked frames, "
+                               "bad pixel map of a master dark (0.1 % hot pixels, 3x3 clumps), correction",
+                   "frames": T, "n": n},
+        "stages_ms": per,
+        "roofline": {"bound": "hbm", "kernel": "sky_subtract", "achieved": sub_bytes / (per["sky_subtract"] / 1e3) / 1e9,
+                     "peak": hbm, "unit": "GB/s",
+                     "frac": sub_bytes / (per["sky_subtract"] / 1e3) / 1e9 / hbm, "traffic": None,
+                     "algorithmic_per_launch": sub_bytes},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # serving loop: Poisson arrivals of full reductions, sizes from the uneven mix
 # ---------------------------------------------------------------------------
 
@@ -730,7 +811,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS) + ["uneven", "serve", "precision"])
+    ap.add_argument("--workload", default="survey",
+                    choices=sorted(WORKLOADS) + ["uneven", "serve", "precision", "prep"])
     ap.add_argument("--no-tune", action="store_true", help="uneven workload: skip the autotuner")
     ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
@@ -755,6 +837,8 @@ def main():
         return run_uneven(args, rank, world, local_rank)
     if args.workload == "precision":
         return run_precision(args, rank, world, local_rank)
+    if args.workload == "prep":
+        return run_prep(args, rank, world, local_rank)
     if args.workload == "serve":
         import torch
         torch.cuda.set_device(local_rank)

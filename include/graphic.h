@@ -186,6 +186,51 @@ int graphic_reduce_host(graphic_ctx *ctx, const float *host_in, int64_t n_frames
 int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_t n, const double *theta_deg,
                            void *stream);
 
+/* ---- image-quality pre-processing (Sect. 3.2) --------------------------------- */
+
+/*
+ * Master sky (Sect. 3.2, "Master sky"): sky(p) = median over the n_frames
+ * frames of the values in[t](p) that are finite and lie outside frame t's
+ * star mask, i.e. not within mask_r pixels of (mask_x[t], mask_y[t]) (x =
+ * column, y = row; mask_x = mask_y = NULL: no mask).  Masked regions may
+ * also be marked by NaN in `in`.  Same median rule as the collapse; NaN
+ * where no value is left.  in: device n_frames x n x n; sky: device n x n;
+ * mask arrays on the host.  Any n_frames >= 1.
+ */
+int graphic_sky_median(graphic_ctx *ctx, const float *in, int64_t n_frames, int32_t n, const double *mask_x,
+                       const double *mask_y, double mask_r, float *sky);
+
+/*
+ * Sky subtraction (Sect. 3.2): out[t] = in[t] - skies[j], j the master sky
+ * closest in time (|sky_times[j] - frame_times[t]| smallest, the lower j on a
+ * tie).  skies: device n_skies x n x n (16-byte aligned); times on the host.
+ * out may equal in.
+ */
+int graphic_sky_subtract(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n,
+                         const float *skies, int32_t n_skies, const double *frame_times, const double *sky_times);
+
+/*
+ * Bad pixel map (Sect. 3.2, "Bad pixel correction"): map[p] = 1 when
+ * |ref[p] - median(ref)| > C sigma, sigma the population standard deviation
+ * of the n x n values of ref (FP64), the median by the rule above (FP32),
+ * the comparison in FP64; else 0.  ref (a master dark or sky) and map
+ * (uint8, n x n) are device buffers.  GRAPHIC_ERR_NONFINITE if ref holds a
+ * non-finite value.
+ */
+int graphic_bad_pixel_map(graphic_ctx *ctx, const float *ref, int32_t n, double C, uint8_t *map);
+
+/*
+ * Bad pixel correction (Sect. 3.2), in place: in every frame the pixels
+ * flagged in map (device n x n uint8, may be NULL) and the non-finite ones
+ * are set to NaN, then, pass after pass, every NaN pixel with at least one
+ * finite 8-neighbour takes the median of those neighbours (same median
+ * rule), all pixels of a pass reading the previous pass's values, until none
+ * is left: clumps fill from their border inwards.  GRAPHIC_ERR_NONFINITE if
+ * a frame has no finite pixel at all (it is left NaN).  Uses the context's
+ * scratch (n_frames x n x n floats).
+ */
+int graphic_bad_pixel_fix(graphic_ctx *ctx, float *cube, int64_t n_frames, int32_t n, const uint8_t *map);
+
 /* ---- uneven batches --------------------------------------------------------- */
 
 /* One cube of a batch: device cubes in/out (n_frames x n x n, out may equal

@@ -65,6 +65,9 @@ struct graphic_ctx {
   int batch_mode = GRAPHIC_BATCH_GROUPED;   // GRAPHIC_BATCH_AUTO resolves to this
   bool group_graph = true;          // grouped executor: record a graph (false: launch directly)
   int precision = GRAPHIC_PREC_FP32;   // line-pass arithmetic for frames of n = 1024
+  // pre-processing: small device buffers (histogram, sums, counters, median, threshold)
+  char *d_prep = nullptr;
+  size_t prep_bytes = 0;
   // graphic_reduce_host: copy stream and event (cube copied in chunks ahead of the shift pass)
   cudaStream_t s_copy = nullptr;
   cudaEvent_t ev_copy = nullptr;
@@ -1224,6 +1227,9 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_counters);
   cudaFree(c->d_gscratch);
   c->d_gscratch = nullptr;
+  cudaFree(c->d_prep);
+  c->d_prep = nullptr;
+  c->prep_bytes = 0;
   c->gscratch_bytes = 0;
   drop_group_graph(c);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -1483,6 +1489,190 @@ int graphic_set_precision(graphic_ctx *c, int32_t precision) {
 int graphic_get_precision(graphic_ctx *c, int32_t *precision) {
   if (!c || !precision) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
   *precision = c->precision;
+  return GRAPHIC_OK;
+}
+
+// --- image-quality pre-processing (Sect. 3.2) ----------------------------------
+int graphic_sky_median(graphic_ctx *c, const float *in, int64_t T, int32_t n, const double *mask_x,
+                       const double *mask_y, double mask_r, float *sky) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, sky, T, n);
+  if (rc) return rc;
+  if (T < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
+  if ((mask_x == nullptr) != (mask_y == nullptr)) return fail(GRAPHIC_ERR_INVALID_ARG, "mask_x and mask_y go together");
+  if (!std::isfinite(mask_r) || mask_r < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "mask_r must be finite, >= 0");
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  size_t o_mx = 0, o_my = 0;
+  if (mask_x) {
+    o_mx = pb.add(mask_x, T * sizeof(double));
+    o_my = pb.add(mask_y, T * sizeof(double));
+  }
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  CollapseArgs a{};
+  a.in = in;
+  a.out = sky;
+  a.status = c->d_status;
+  a.T = T;
+  a.n = n;
+  a.mask_x = mask_x ? at<double>(c, o_mx) : nullptr;
+  a.mask_y = mask_x ? at<double>(c, o_my) : nullptr;
+  a.mask_r2 = mask_r * mask_r;
+  prof_begin(c, GRAPHIC_K_COLLAPSE);
+  cudaError_t e = launch_sky_median(a, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "sky median kernel");
+  return end_call(c);
+}
+
+int graphic_sky_subtract(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const float *skies,
+                         int32_t n_skies, const double *frame_times, const double *sky_times) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if (n_skies < 1 || !skies || ((uintptr_t)skies & 15)) return fail(GRAPHIC_ERR_INVALID_ARG, "need >= 1 aligned sky");
+  if (T > 0 && (!frame_times || !sky_times)) return fail(GRAPHIC_ERR_INVALID_ARG, "null times");
+  std::vector<int> j(T, 0);
+  for (int64_t t = 0; t < T; t++) {
+    if (!std::isfinite(frame_times[t])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite time");
+    for (int s = 1; s < n_skies; s++)
+      if (fabs(sky_times[s] - frame_times[t]) < fabs(sky_times[j[t]] - frame_times[t])) j[t] = s;
+  }
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_j = pb.add(j.data(), T * sizeof(int));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  cudaError_t e = launch_sky_subtract(in, out, T, n, skies, at<int>(c, o_j), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sky subtraction kernel");
+  return end_call(c);
+}
+
+namespace {
+
+// host value of a total-order key
+float key_value(uint32_t key) {
+  const uint32_t b = (key & 0x80000000u) ? (key & 0x7fffffffu) : ~key;
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+}
+
+// Key of the k-th smallest (0-based) of n_vals device floats: four radix
+// passes, each a device histogram read back by the host.
+int select_key(graphic_ctx *c, const float *v, long long n_vals, unsigned long long k, unsigned int *d_hist,
+               uint32_t *key) {
+  uint32_t prefix = 0, pmask = 0;
+  unsigned long long krem = k;
+  std::vector<unsigned int> h(256);
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 24 - 8 * pass;
+    cudaError_t e = launch_key_histogram(v, n_vals, prefix, pmask, shift, d_hist, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_hist, 256 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                              c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "frame median");
+    unsigned long long cum = 0;
+    int d = 255;
+    for (int b = 0; b < 256; b++) {
+      if (cum + h[b] > krem) {
+        d = b;
+        break;
+      }
+      cum += h[b];
+    }
+    krem -= cum;
+    prefix |= (uint32_t)d << shift;
+    pmask |= 0xffu << shift;
+  }
+  *key = prefix;
+  return GRAPHIC_OK;
+}
+
+}  // namespace
+
+int graphic_bad_pixel_map(graphic_ctx *c, const float *ref, int32_t n, double C, uint8_t *map) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (!ref || !map || n < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "null buffer or n < 1");
+  if (!std::isfinite(C) || C < 0) return fail(GRAPHIC_ERR_INVALID_ARG, "C must be finite, >= 0");
+  DeviceGuard g(c->device);
+  const long long N = (long long)n * n;
+  int rc;
+  if ((rc = ensure((void **)&c->d_prep, &c->prep_bytes, 4096, false))) return rc;
+  unsigned int *d_hist = reinterpret_cast<unsigned int *>(c->d_prep);          // 1 KB
+  double *d_sums = reinterpret_cast<double *>(c->d_prep + 1024);              // 2 doubles
+  double *d_mean = d_sums + 2;
+  double *d_thresh = d_sums + 3;
+  float *d_med = reinterpret_cast<float *>(c->d_prep + 1024 + 64);
+  double sums[2] = {0, 0};
+  CK(cudaMemsetAsync(d_sums, 0, 2 * sizeof(double), c->stream));
+  cudaError_t e = launch_frame_sums(ref, N, nullptr, d_sums, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frame sums");
+  CK(cudaMemcpyAsync(sums, d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (!std::isfinite(sums[0])) return fail(GRAPHIC_ERR_NONFINITE, "non-finite value in the reference frame");
+  const double mean = sums[0] / (double)N;
+  CK(cudaMemcpyAsync(d_mean, &mean, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  e = launch_frame_sums(ref, N, d_mean, d_sums, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "frame sums");
+  CK(cudaMemcpyAsync(sums, d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const double sigma = sqrt(sums[1] / (double)N);
+  uint32_t klo, khi;
+  if ((rc = select_key(c, ref, N, (unsigned long long)((N - 1) / 2), d_hist, &klo))) return rc;
+  float med = key_value(klo);
+  if ((N & 1) == 0) {
+    if ((rc = select_key(c, ref, N, (unsigned long long)(N / 2), d_hist, &khi))) return rc;
+    const float hi = key_value(khi);
+    volatile float s = med + hi;   // FP32 sum, then the halving, as the device medians
+    med = s * 0.5f;
+  }
+  const double thresh = C * sigma;
+  CK(cudaMemcpyAsync(d_med, &med, sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d_thresh, &thresh, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  e = launch_bad_map(ref, N, d_med, d_thresh, map, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bad pixel map kernel");
+  CK(cudaStreamSynchronize(c->stream));
+  return GRAPHIC_OK;
+}
+
+int graphic_bad_pixel_fix(graphic_ctx *c, float *cube, int64_t T, int32_t n, const uint8_t *map) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (T < 0 || (T > 0 && !cube) || n < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "bad cube");
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  const size_t bytes = (size_t)T * n * n * sizeof(float);
+  int rc;
+  if ((rc = ensure((void **)&c->d_prep, &c->prep_bytes, 4096, false))) return rc;
+  if ((rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, bytes, false))) return rc;
+  unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(c->d_prep + 2048);   // [3]
+  unsigned long long cnt[3] = {0, 0, 0};
+  CK(cudaMemsetAsync(d_cnt, 0, 3 * sizeof(unsigned long long), c->stream));
+  cudaError_t e = launch_bad_mark(cube, T, n, map, d_cnt, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bad pixel marking kernel");
+  CK(cudaMemcpyAsync(cnt, d_cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned long long left = cnt[0];
+  float *src = cube, *dst = c->d_scratch;
+  bool hopeless = false;
+  for (int pass = 0; left > 0 && pass <= 2 * n; pass++) {
+    CK(cudaMemsetAsync(d_cnt + 1, 0, 2 * sizeof(unsigned long long), c->stream));
+    e = launch_bad_pass(src, dst, T, n, d_cnt + 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bad pixel pass kernel");
+    CK(cudaMemcpyAsync(cnt + 1, d_cnt + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::swap(src, dst);
+    if (cnt[2] == 0) {
+      hopeless = true;
+      break;
+    }
+    left = cnt[1];
+  }
+  if (src != cube) CK(cudaMemcpyAsync(cube, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (hopeless || left > 0) return fail(GRAPHIC_ERR_NONFINITE, "a frame has no finite pixel left to fill from");
   return GRAPHIC_OK;
 }
 

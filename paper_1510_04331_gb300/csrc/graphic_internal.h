@@ -157,7 +157,30 @@ struct CollapseArgs {
   int *status;
   long long T;
   int n;
+  // master-sky variant (launch_sky_median): values that are not finite or
+  // lie within mask_r of the frame's (mask_x[t], mask_y[t]) are left out
+  const double *mask_x;  // [T] device, may be null (no mask)
+  const double *mask_y;
+  double mask_r2;
 };
 cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st);
+cudaError_t launch_sky_median(const CollapseArgs &a, cudaStream_t st);
+
+// prep.cu: image-quality pre-processing (Sect. 3.2)
+cudaError_t launch_sky_subtract(const float *in, float *out, long long T, int n, const float *skies,
+                                const int *sky_of_frame, cudaStream_t st);
+// one radix pass over the keys of n_vals floats: histogram (256 bins, device,
+// zeroed here) of digit `shift` among keys whose bits under pmask equal prefix
+cudaError_t launch_key_histogram(const float *v, long long n_vals, uint32_t prefix, uint32_t pmask, int shift,
+                                 unsigned int *hist, cudaStream_t st);
+// FP64 sums: sums[0] += v, or with mean != null sums[1] += (v - *mean)^2
+cudaError_t launch_frame_sums(const float *v, long long n_vals, const double *mean, double *sums, cudaStream_t st);
+cudaError_t launch_bad_map(const float *ref, long long n_vals, const float *med, const double *thresh,
+                           uint8_t *map, cudaStream_t st);
+// bad pixel correction: mark (flagged or non-finite -> NaN), then passes
+cudaError_t launch_bad_mark(float *cube, long long T, int n, const uint8_t *map, unsigned long long *nan_count,
+                            cudaStream_t st);
+cudaError_t launch_bad_pass(const float *src, float *dst, long long T, int n, unsigned long long *counts,
+                            cudaStream_t st);
 
 }  // namespace graphic

@@ -153,7 +153,11 @@ __device__ __forceinline__ void hist_find(const uint32_t *hist, uint32_t krem, i
 constexpr int COL_PPC = 4;
 constexpr int COL_KS = 5;
 
-template <bool SMEM>
+// MASKED (master sky, Sect. 3.2): values that are not finite or fall in the
+// frame's star mask are left out -- they get the largest key, so they rank
+// after every value kept -- and the median is taken over the m values kept
+// (NaN when m = 0).
+template <bool SMEM, bool MASKED = false>
 __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
   uint32_t *hist_all = csm;                       // [COL_PPC][256]
@@ -175,25 +179,35 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
   }
   uint32_t *hist = hist_all + w * 256;
   const long long p = p0 + w;
+  // masked-out values (MASKED) get the largest key
+  auto key_of = [&](long long t, float v) -> uint32_t {
+    if constexpr (MASKED) {
+      bool keep = isfinite(v);
+      if (a.mask_x) {
+        const double ddx = (double)(p % a.n) - a.mask_x[t], ddy = (double)(p / a.n) - a.mask_y[t];
+        keep &= !(ddx * ddx + ddy * ddy < a.mask_r2);
+      }
+      return keep ? f2key(v) : 0xffffffffu;
+    } else {
+      return f2key(v);
+    }
+  };
   auto key_at = [&](long long t) -> uint32_t {
     if constexpr (SMEM) return keys_all[t * COL_KS + w];
-    else return f2key(a.in[t * NN + p]);
+    else return key_of(t, a.in[t * NN + p]);
   };
   // keys in place (each warp converts its own pixel), finiteness, and the
   // digits shared by every key
   uint32_t orv = 0, andv = 0xffffffffu;
+  int kept = 0;
   for (long long t = lane; t < T; t += 32) {
-    uint32_t key;
-    if constexpr (SMEM) {
-      const float v = __uint_as_float(keys_all[t * COL_KS + w]);
-      bad |= !isfinite(v);
-      key = f2key(v);
-      keys_all[t * COL_KS + w] = key;
-    } else {
-      const float v = a.in[t * NN + p];
-      bad |= !isfinite(v);
-      key = f2key(v);
-    }
+    float v;
+    if constexpr (SMEM) v = __uint_as_float(keys_all[t * COL_KS + w]);
+    else v = a.in[t * NN + p];
+    const uint32_t key = key_of(t, v);
+    if constexpr (MASKED) kept += (key != 0xffffffffu) ? 1 : 0;
+    else bad |= !isfinite(v);
+    if constexpr (SMEM) keys_all[t * COL_KS + w] = key;
     orv |= key;
     andv &= key;
   }
@@ -206,7 +220,17 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
   __syncwarp();
   const uint32_t varying = orv ^ andv;
 
-  const uint32_t k = (uint32_t)((T - 1) / 2);
+  long long m = T;
+  if constexpr (MASKED) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+    m = kept;
+    if (m == 0) {
+      if (lane == 0) a.out[p] = __uint_as_float(0x7fc00000u);   // no value left: NaN
+      return;
+    }
+  }
+  const uint32_t k = (uint32_t)((m - 1) / 2);
   uint32_t prefix = 0, pmask = 0, krem = k, cnt = (uint32_t)T;
   for (int pass = 0; pass < 4; pass++) {
     const int shift = 24 - 8 * pass;
@@ -233,18 +257,18 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
   }
   const float lo = key2f(prefix);
   float med = lo;
-  if ((T & 1) == 0) {
+  if ((m & 1) == 0) {
     uint32_t hi = prefix;
     if (krem + 1 >= cnt) {
       // smallest key greater than the lower median
-      uint32_t m = 0xffffffffu;
+      uint32_t mn = 0xffffffffu;
       for (long long t = lane; t < T; t += 32) {
         const uint32_t key = key_at(t);
-        if (key > prefix && key < m) m = key;
+        if (key > prefix && key < mn) mn = key;
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL, m, o));
-      hi = m;
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+      hi = mn;
     }
     med = (lo + key2f(hi)) * 0.5f;
   }
@@ -1013,6 +1037,22 @@ cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
   } else {
     const size_t smem = (size_t)(COL_PPC * 256) * sizeof(uint32_t);
     collapse_kernel<false><<<grid, 32 * COL_PPC, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sky_median(const CollapseArgs &a, cudaStream_t st) {
+  const long long NN = (long long)a.n * a.n;
+  const unsigned grid = (unsigned)(NN / COL_PPC);
+  if (a.T <= 8192) {
+    const size_t smem = (size_t)(COL_PPC * 256 + COL_KS * a.T) * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(collapse_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    collapse_kernel<true, true><<<grid, 32 * COL_PPC, smem, st>>>(a);
+  } else {
+    const size_t smem = (size_t)(COL_PPC * 256) * sizeof(uint32_t);
+    collapse_kernel<false, true><<<grid, 32 * COL_PPC, smem, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -115,6 +115,10 @@ _SIGS = {
                                 _D, _I32],
     "graphic_reduce_ex": [_P, _P, _P, _I64, _I32, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
                           ctypes.c_double, _D, _I32, _P],
+    "graphic_sky_median": [_P, _P, _I64, _I32, _D, _D, ctypes.c_double, _P],
+    "graphic_sky_subtract": [_P, _P, _P, _I64, _I32, _P, _I32, _D, _D],
+    "graphic_bad_pixel_map": [_P, _P, _I32, ctypes.c_double, _P],
+    "graphic_bad_pixel_fix": [_P, _P, _I64, _I32, _P],
     "graphic_reduce_host": [_P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
     "graphic_profile": [_P, ctypes.c_int],
     "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
@@ -342,6 +346,57 @@ class Context:
         k = len(SCHEDULE_KEYS)
         v = (_I32 * k)(*[int(cur[key]) for key in SCHEDULE_KEYS])
         _check(lib().graphic_set_schedule(self.h, v, k))
+
+    # --- image-quality pre-processing (Sect. 3.2) ---------------------------
+    def graphic_sky_median(self, cube, mask_x=None, mask_y=None, mask_r=0.0, out=None):
+        """Master sky: per-pixel median of the finite values outside each
+        frame's star mask (NaN where none is left); returns an n x n tensor."""
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty((n, n), dtype=torch.float32, device=cube.device) if out is None else out
+        mxa, pmx = (None, None) if mask_x is None else _f64(mask_x, T)
+        mya, pmy = (None, None) if mask_y is None else _f64(mask_y, T)
+        self._stream()
+        _check(lib().graphic_sky_median(self.h, _P(cube.data_ptr()), T, n, pmx, pmy, float(mask_r),
+                                        _P(out.data_ptr())))
+        return out
+
+    def graphic_sky_subtract(self, cube, skies, frame_times, sky_times, out=None):
+        """Each frame minus the master sky closest in time."""
+        import torch
+        cube = _cube(cube)
+        skies = _cube(skies, "skies")
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty_like(cube) if out is None else _cube(out, "out")
+        fta, pft = _f64(frame_times, T)
+        sta, pst = _f64(sky_times, skies.shape[0])
+        self._stream()
+        _check(lib().graphic_sky_subtract(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n,
+                                          _P(skies.data_ptr()), skies.shape[0], pft, pst))
+        return out
+
+    def graphic_bad_pixel_map(self, ref, C):
+        """uint8 n x n map of the pixels of ref farther than C sigma from its median."""
+        import torch
+        if not (isinstance(ref, torch.Tensor) and ref.is_cuda and ref.dtype == torch.float32 and ref.dim() == 2
+                and ref.is_contiguous() and ref.shape[0] == ref.shape[1]):
+            raise GraphicError(-1, "ref must be a contiguous CUDA float32 n x n tensor")
+        n = ref.shape[0]
+        out = torch.empty((n, n), dtype=torch.uint8, device=ref.device)
+        self._stream()
+        _check(lib().graphic_bad_pixel_map(self.h, _P(ref.data_ptr()), n, float(C), _P(out.data_ptr())))
+        return out
+
+    def graphic_bad_pixel_fix(self, cube, bad_map=None):
+        """In place: flagged and non-finite pixels replaced by the median of
+        their finite 8-neighbours, pass by pass."""
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        self._stream()
+        _check(lib().graphic_bad_pixel_fix(self.h, _P(cube.data_ptr()), T, n,
+                                           None if bad_map is None else _P(bad_map.data_ptr())))
+        return cube
 
     def set_precision(self, precision: int):
         """PREC_FP32 (default), PREC_BF16X3 or PREC_FP16X3: arithmetic of the
