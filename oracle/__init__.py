@@ -23,6 +23,7 @@ Functions and the passages they follow:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -94,6 +95,12 @@ def _load():
                                                     _d]
             lib.oracle_bad_pixel_map_f32.argtypes = [_f, ctypes.c_int, ctypes.c_double, _u8]
             lib.oracle_bad_pixel_fix_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, _u8]
+            lib.oracle_centroid_frame_f32.argtypes = [_f, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int, _d, _d, ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_moffat_fit_f32.argtypes = [_f, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int, _d]
+            lib.oracle_moffat_fwhm.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.oracle_moffat_fwhm.restype = ctypes.c_double
             lib.oracle_last_max_imag.restype = ctypes.c_double
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -331,3 +338,50 @@ def bad_pixel_fix(cube, bad_map=None):
     m = None if bad_map is None else np.ascontiguousarray(bad_map, dtype=np.uint8)
     st = _load().oracle_bad_pixel_fix_f32(_p(c, _f), T, N, None if m is None else _p(m, _u8))
     return c, st
+
+
+# --------------------------------------------------------------------------
+# Registration (Sect. 3.1): centroid patch search, Moffat fit
+# --------------------------------------------------------------------------
+
+def centroid(frame, thresh: float, R: int, min_size: int, max_size: int):
+    """(found, cx, cy, patch size) of one frame."""
+    f = _f32(frame)
+    N = f.shape[0]
+    cx, cy, sz = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    found = _load().oracle_centroid_frame_f32(_p(f, _f), N, float(thresh), int(R), int(min_size), int(max_size),
+                                              ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(sz))
+    return bool(found), cx.value, cy.value, sz.value
+
+
+def moffat_fit(frame, cx: float, cy: float, alpha0: float, w: int):
+    """Levenberg-Marquardt Moffat fit: (p = [I0, x0, y0, alpha, beta, Bg], iterations)."""
+    f = _f32(frame)
+    N = f.shape[0]
+    p = np.zeros(6)
+    it = _load().oracle_moffat_fit_f32(_p(f, _f), N, float(cx), float(cy), float(alpha0), int(w), _p(p, _d))
+    return p, it
+
+
+def moffat_fwhm(alpha: float, beta: float) -> float:
+    return _load().oracle_moffat_fwhm(float(alpha), float(beta))
+
+
+def register(cube, thresh: float, R: int, min_size: int, max_size: int, w: int):
+    """Per frame: centroid, then the Moffat fit started there with alpha0 =
+    max(1, sqrt(patch size / pi)).  Returns arrays found, x0, y0, fwhm
+    (NaN where no centroid was found)."""
+    c = _f32(cube)
+    T = c.shape[0]
+    found = np.zeros(T, bool)
+    x0 = np.full(T, np.nan)
+    y0 = np.full(T, np.nan)
+    fw = np.full(T, np.nan)
+    for t in range(T):
+        ok, cx, cy, sz = centroid(c[t], thresh, R, min_size, max_size)
+        if not ok:
+            continue
+        p, _ = moffat_fit(c[t], cx, cy, max(1.0, math.sqrt(sz / math.pi)), w)
+        found[t] = True
+        x0[t], y0[t], fw[t] = p[1], p[2], moffat_fwhm(p[3], p[4])
+    return found, x0, y0, fw

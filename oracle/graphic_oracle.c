@@ -730,3 +730,211 @@ int oracle_bad_pixel_fix_f32(float *cube, long long T, int N, const unsigned cha
     }
     return status;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Registration (Sect. 3.1): centroid patch search and Moffat fit          */
+/* ---------------------------------------------------------------------- */
+
+/* Exported: centroid search of one frame (Sect. 3.1, "searches for a patch
+ * of contiguous pixels above a given threshold value"): the seed is the
+ * brightest pixel (the first in row-major order on a tie); the patch is the
+ * 8-connected set of pixels with value > thresh reachable from the seed
+ * inside the box of half-size R around it (clipped to the frame).  The
+ * centroid is found when the seed is above thresh, the patch touches no box
+ * edge that lies inside the frame (else it may continue beyond the box) and
+ * min_size <= |patch| <= max_size; it is then the flux-weighted centre of
+ * mass sum v (x, y) / sum v of the patch (x = column, y = row, FP64).
+ * Returns found (0/1); *size receives |patch|. */
+int oracle_centroid_frame_f32(const float *f, int N, double thresh, int R, int min_size, int max_size, double *cx,
+                              double *cy, int *size)
+{
+    size_t NN = (size_t)N * N, best = 0;
+    for (size_t p = 1; p < NN; p++)
+        if (f[p] > f[best]) best = p;
+    int r0 = (int)(best / N), c0 = (int)(best % N);
+    int rlo = r0 - R < 0 ? 0 : r0 - R, rhi = r0 + R >= N ? N - 1 : r0 + R;
+    int clo = c0 - R < 0 ? 0 : c0 - R, chi = c0 + R >= N ? N - 1 : c0 + R;
+    int H = rhi - rlo + 1, W = chi - clo + 1;
+    *size = 0;
+    *cx = *cy = 0.0;
+    if (!((double)f[best] > thresh)) return 0;
+    unsigned char *lab = (unsigned char *)calloc((size_t)H * W, 1);
+    int *stack = (int *)malloc(sizeof(int) * (size_t)H * W);
+    int top = 0, n = 0, touch = 0;
+    double sv = 0.0, sx = 0.0, sy = 0.0;
+    lab[(size_t)(r0 - rlo) * W + (c0 - clo)] = 1;
+    stack[top++] = (r0 - rlo) * W + (c0 - clo);
+    while (top > 0) {
+        int q = stack[--top];
+        int r = q / W, c = q % W;
+        double v = (double)f[(size_t)(r + rlo) * N + (c + clo)];
+        n++;
+        sv += v;
+        sx += v * (double)(c + clo);
+        sy += v * (double)(r + rlo);
+        if ((r == 0 && rlo > 0) || (r == H - 1 && rhi < N - 1) || (c == 0 && clo > 0) || (c == W - 1 && chi < N - 1))
+            touch = 1;
+        for (int dr = -1; dr <= 1; dr++)
+            for (int dc = -1; dc <= 1; dc++) {
+                int rr = r + dr, cc = c + dc;
+                if ((!dr && !dc) || rr < 0 || rr >= H || cc < 0 || cc >= W) continue;
+                size_t k = (size_t)rr * W + cc;
+                if (lab[k]) continue;
+                if ((double)f[(size_t)(rr + rlo) * N + (cc + clo)] > thresh) {
+                    lab[k] = 1;
+                    stack[top++] = (int)k;
+                }
+            }
+    }
+    free(lab);
+    free(stack);
+    *size = n;
+    if (touch || n < min_size || n > max_size) return 0;
+    *cx = sx / sv;
+    *cy = sy / sv;
+    return 1;
+}
+
+/* Moffat model (Sect. 3.1) and its partial derivatives in the parameters
+ * p = (I0, x0, y0, alpha, beta, Bg) at pixel (x, y). */
+static double moffat_eval(const double *p, double x, double y, double *grad)
+{
+    double I0 = p[0], x0 = p[1], y0 = p[2], al = p[3], be = p[4];
+    double dx = x - x0, dy = y - y0, rho2 = dx * dx + dy * dy;
+    double u = 1.0 + rho2 / (al * al);
+    double P = exp(-be * log(u));
+    double A = I0 * (be - 1.0) / (ORACLE_PI * al * al);
+    if (grad) {
+        double Pu = P / u;   /* u^(-beta-1) */
+        grad[0] = (be - 1.0) / (ORACLE_PI * al * al) * P;
+        grad[1] = A * be * Pu * 2.0 * dx / (al * al);
+        grad[2] = A * be * Pu * 2.0 * dy / (al * al);
+        grad[3] = -2.0 * A / al * P + A * 2.0 * be * rho2 * Pu / (al * al * al);
+        grad[4] = I0 / (ORACLE_PI * al * al) * P - A * log(u) * P;
+        grad[5] = 1.0;
+    }
+    return A * P + p[5];
+}
+
+static double moffat_cost(const double *p, const float *f, int N, int r0, int r1, int c0, int c1)
+{
+    double s = 0.0;
+    for (int r = r0; r <= r1; r++)
+        for (int c = c0; c <= c1; c++) {
+            double e = moffat_eval(p, (double)c, (double)r, NULL) - (double)f[(size_t)r * N + c];
+            s += e * e;
+        }
+    return s;
+}
+
+/* 6 x 6 symmetric positive definite solve by Cholesky; 0 on failure. */
+static int chol6(const double *A, const double *b, double *x)
+{
+    double L[36] = {0};
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j <= i; j++) {
+            double s = A[i * 6 + j];
+            for (int k = 0; k < j; k++) s -= L[i * 6 + k] * L[j * 6 + k];
+            if (i == j) {
+                if (!(s > 0)) return 0;
+                L[i * 6 + i] = sqrt(s);
+            } else {
+                L[i * 6 + j] = s / L[j * 6 + j];
+            }
+        }
+    double y[6];
+    for (int i = 0; i < 6; i++) {
+        double s = b[i];
+        for (int k = 0; k < i; k++) s -= L[i * 6 + k] * y[k];
+        y[i] = s / L[i * 6 + i];
+    }
+    for (int i = 5; i >= 0; i--) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; k++) s -= L[k * 6 + i] * x[k];
+        x[i] = s / L[i * 6 + i];
+    }
+    return 1;
+}
+
+/* Exported: Moffat fit of one frame (Sect. 3.1) by Levenberg-Marquardt over
+ * the window of half-size w around the rounded initial centre (clipped to
+ * the frame).  Start: (x0, y0) = (cx, cy), Bg = window minimum, beta = 2.5,
+ * alpha = alpha0, I0 = sum over the window of (v - Bg).  Iteration: normal
+ * equations of the analytic Jacobian, damped by lambda * diag (lambda from
+ * 1e-3, /10 on an accepted step, *10 on a rejected one or on alpha <= 0,
+ * beta <= 1), stop when an accepted step lowers the cost by less than 1e-14
+ * of it, when no damping up to 10 tries lowers it, or after 200 iterations.
+ * p_out = (I0, x0, y0, alpha, beta, Bg); returns the iterations made. */
+int oracle_moffat_fit_f32(const float *f, int N, double cx, double cy, double alpha0, int w, double *p_out)
+{
+    int rc_ = (int)floor(cy + 0.5), cc_ = (int)floor(cx + 0.5);
+    int r0 = rc_ - w < 0 ? 0 : rc_ - w, r1 = rc_ + w >= N ? N - 1 : rc_ + w;
+    int c0 = cc_ - w < 0 ? 0 : cc_ - w, c1 = cc_ + w >= N ? N - 1 : cc_ + w;
+    double bg = (double)f[(size_t)r0 * N + c0];
+    for (int r = r0; r <= r1; r++)
+        for (int c = c0; c <= c1; c++) bg = fmin(bg, (double)f[(size_t)r * N + c]);
+    double I0 = 0.0;
+    for (int r = r0; r <= r1; r++)
+        for (int c = c0; c <= c1; c++) I0 += (double)f[(size_t)r * N + c] - bg;
+    double p[6] = {I0, cx, cy, alpha0, 2.5, bg};
+    double lambda = 1e-3;
+    double cost = moffat_cost(p, f, N, r0, r1, c0, c1);
+    int it;
+    for (it = 0; it < 200; it++) {
+        double JJ[36] = {0}, g[6] = {0};
+        for (int r = r0; r <= r1; r++)
+            for (int c = c0; c <= c1; c++) {
+                double gr[6];
+                double e = moffat_eval(p, (double)c, (double)r, gr) - (double)f[(size_t)r * N + c];
+                for (int i = 0; i < 6; i++) {
+                    g[i] += gr[i] * e;
+                    for (int j = 0; j <= i; j++) JJ[i * 6 + j] += gr[i] * gr[j];
+                }
+            }
+        for (int i = 0; i < 6; i++)
+            for (int j = 0; j < i; j++) JJ[j * 6 + i] = JJ[i * 6 + j];
+        int accepted = 0;
+        double newcost = cost;
+        for (int tries = 0; tries < 10; tries++) {
+            double A[36], mg[6], d[6], q[6];
+            for (int i = 0; i < 36; i++) A[i] = JJ[i];
+            for (int i = 0; i < 6; i++) {
+                double di = JJ[i * 6 + i] > 0 ? JJ[i * 6 + i] : 1e-12;
+                A[i * 6 + i] += lambda * di;
+                mg[i] = -g[i];
+            }
+            if (!chol6(A, mg, d)) {
+                lambda *= 10.0;
+                continue;
+            }
+            for (int i = 0; i < 6; i++) q[i] = p[i] + d[i];
+            if (!(q[3] > 0) || !(q[4] > 1.0)) {
+                lambda *= 10.0;
+                continue;
+            }
+            newcost = moffat_cost(q, f, N, r0, r1, c0, c1);
+            if (newcost < cost) {
+                for (int i = 0; i < 6; i++) p[i] = q[i];
+                lambda = fmax(lambda / 10.0, 1e-12);
+                accepted = 1;
+                break;
+            }
+            lambda *= 10.0;
+        }
+        if (!accepted) break;
+        double drop = cost - newcost;
+        cost = newcost;
+        if (drop <= 1e-14 * cost) {
+            it++;
+            break;
+        }
+    }
+    for (int i = 0; i < 6; i++) p_out[i] = p[i];
+    return it;
+}
+
+/* FWHM of the Moffat profile (Sect. 3.1): 2 alpha sqrt(2^(1/beta) - 1). */
+double oracle_moffat_fwhm(double alpha, double beta)
+{
+    return 2.0 * alpha * sqrt(pow(2.0, 1.0 / beta) - 1.0);
+}

@@ -537,3 +537,57 @@ def test_bad_pixel_fix_constant_frame_and_hopeless_frame():
     got, st = oracle.bad_pixel_fix(f)
     assert np.array_equal(got[0], np.full((6, 6), 3.25, np.float32))
     assert st == 1                                        # frame 1 has no finite pixel
+
+
+# --------------------------------------------------------------------------
+# Registration (Sect. 3.1): centroid patch search, Moffat fit
+# --------------------------------------------------------------------------
+
+def _moffat_image(N, I0, x0, y0, al, be, bg):
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    u = 1.0 + ((xx - x0) ** 2 + (yy - y0) ** 2) / al ** 2
+    return (I0 * (be - 1.0) / (math.pi * al * al) * u ** (-be) + bg).astype(np.float32)
+
+
+def test_moffat_fit_recovers_noise_free_parameters():
+    truth = (5e4, 31.3, 29.7, 3.1, 2.7, 12.0)
+    img = _moffat_image(64, *truth)
+    ok, cx, cy, sz = oracle.centroid(img, 12.0 + 0.05 * img.max(), 16, 4, 400)
+    assert ok
+    p, it = oracle.moffat_fit(img, cx, cy, max(1.0, math.sqrt(sz / math.pi)), 12)
+    assert abs(p[1] - 31.3) < 1e-5 and abs(p[2] - 29.7) < 1e-5
+    assert abs(p[3] / 3.1 - 1) < 1e-5 and abs(p[4] / 2.7 - 1) < 1e-5 and abs(p[0] / 5e4 - 1) < 1e-5
+    assert abs(p[5] - 12.0) < 1e-3
+
+
+def test_moffat_fwhm_is_the_width_at_half_maximum():
+    # independent route: bisection for the radius where the profile halves
+    for al, be in ((3.1, 2.7), (1.2, 1.5), (6.0, 8.0)):
+        lo, hi = 0.0, 100.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if (1.0 + mid * mid / (al * al)) ** (-be) > 0.5:
+                lo = mid
+            else:
+                hi = mid
+        assert abs(oracle.moffat_fwhm(al, be) - 2.0 * lo) < 1e-12
+
+
+def test_moffat_fit_follows_integer_translations():
+    a = _moffat_image(64, 3e4, 30.4, 33.2, 2.5, 3.0, 5.0)
+    b = np.roll(np.roll(a, 3, axis=1), -2, axis=0)        # content moves by (+3, -2); far from the edges
+    pa, _ = oracle.moffat_fit(a, 30.0, 33.0, 2.0, 10)
+    pb, _ = oracle.moffat_fit(b, 33.0, 31.0, 2.0, 10)
+    assert abs(pb[1] - pa[1] - 3.0) < 1e-6 and abs(pb[2] - pa[2] + 2.0) < 1e-6
+
+
+def test_centroid_of_a_symmetric_patch_and_its_flags():
+    f = np.zeros((32, 32), np.float32)
+    f[10, 20] = 9.0
+    f[9, 20] = f[11, 20] = f[10, 19] = f[10, 21] = 4.0        # plus-shaped patch centred on (x, y) = (20, 10)
+    ok, cx, cy, sz = oracle.centroid(f, 1.0, 5, 3, 10)
+    assert ok and cx == 20.0 and cy == 10.0 and sz == 5
+    assert not oracle.centroid(f, 10.0, 5, 3, 10)[0]          # seed below the threshold
+    assert not oracle.centroid(f, 1.0, 5, 6, 10)[0]           # patch too small
+    assert not oracle.centroid(f, 1.0, 5, 1, 4)[0]            # patch too large
+    assert not oracle.centroid(f, 1.0, 0, 1, 10)[0]           # patch reaches the box edge
