@@ -231,6 +231,38 @@ int graphic_bad_pixel_map(graphic_ctx *ctx, const float *ref, int32_t n, double 
  */
 int graphic_bad_pixel_fix(graphic_ctx *ctx, float *cube, int64_t n_frames, int32_t n, const uint8_t *map);
 
+/*
+ * Registration (Sect. 3.1): per frame of the device cube in (n_frames x n x
+ * n floats, any n >= 1), the star's centre and FWHM.
+ *  1. Centroid: the seed is the brightest pixel (the first in row-major
+ *     order on a tie); the patch is the 8-connected set of pixels above
+ *     thresh reachable from it inside the box of half-size R around it
+ *     (clipped to the frame).  The frame is registered when the seed is
+ *     above thresh, the patch touches no box edge that lies inside the
+ *     frame and min_size <= |patch| <= max_size; the centroid is the
+ *     flux-weighted centre of mass of the patch (x = column, y = row).
+ *  2. Moffat fit I(x, y) = I0 (beta - 1) / (pi alpha^2) (1 + rho^2 /
+ *     alpha^2)^(-beta) + Bg, rho the distance to (x0, y0), by
+ *     Levenberg-Marquardt over the window of half-size w around the rounded
+ *     centroid (clipped): start x0, y0 = centroid, alpha = max(1,
+ *     sqrt(|patch| / pi)), beta = 2.5, Bg = window minimum, I0 = sum of (v -
+ *     Bg) over the window; damping lambda * diag(J^T J) from lambda = 1e-3
+ *     (/10 on an accepted step, *10 on a rejected one or one leaving alpha
+ *     <= 0 or beta <= 1, at most 10 tries); stop when an accepted step
+ *     lowers the squared error by at most 1e-14 of it, when no try lowers
+ *     it, or after 200 iterations.  FWHM = 2 alpha sqrt(2^(1/beta) - 1).
+ * out: device n_frames x 8 doubles per frame: found (1.0 / 0.0), x0, y0,
+ * FWHM, I0, alpha, beta, Bg (all 0 when not found).  iters: device
+ * n_frames int32 (iterations made, 0 when not found) or NULL.  in must be
+ * 16-byte aligned, 1 <= n <= 65535, 1 <= R <= 32, 1 <= w <= 32; the
+ * context scratch holds 8 bytes a frame.  All arithmetic after the pixel
+ * values is FP64.  GRAPHIC_ERR_NONFINITE if a frame holds a non-finite
+ * value (its row of out is then zero).  Two kernel launches (frame
+ * argmax, fit); synchronous.
+ */
+int graphic_register(graphic_ctx *ctx, const float *in, int64_t n_frames, int32_t n, double thresh, int32_t R,
+                     int32_t min_size, int32_t max_size, int32_t w, double *out, int32_t *iters);
+
 /* ---- uneven batches --------------------------------------------------------- */
 
 /* One cube of a batch: device cubes in/out (n_frames x n x n, out may equal
@@ -333,7 +365,9 @@ int graphic_get_precision(graphic_ctx *ctx, int32_t *precision);
 #define GRAPHIC_K_ROT_P3 5
 #define GRAPHIC_K_COLLAPSE 6
 #define GRAPHIC_K_BATCH 7
-#define GRAPHIC_K_COUNT 8
+#define GRAPHIC_K_REG_ARGMAX 8
+#define GRAPHIC_K_REG_FIT 9
+#define GRAPHIC_K_COUNT 10
 
 /* enable != 0: bracket every kernel launch of the context with CUDA events
  * on its stream and accumulate per-kernel device time and launch counts;

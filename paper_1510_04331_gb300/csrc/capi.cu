@@ -1676,6 +1676,43 @@ int graphic_bad_pixel_fix(graphic_ctx *c, float *cube, int64_t T, int32_t n, con
   return GRAPHIC_OK;
 }
 
+int graphic_register(graphic_ctx *c, const float *in, int64_t T, int32_t n, double thresh, int32_t R,
+                     int32_t min_size, int32_t max_size, int32_t w, double *out, int32_t *iters) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (T < 0 || T > (int64_t)INT32_MAX * 4 || n < 1 || n > 65535) return fail(GRAPHIC_ERR_INVALID_ARG, "bad cube shape");
+  if (T > 0 && (!in || !out)) return fail(GRAPHIC_ERR_INVALID_ARG, "null buffer");
+  if ((uintptr_t)in & 15) return fail(GRAPHIC_ERR_INVALID_ARG, "the cube must be 16-byte aligned");
+  if (R < 1 || R > 32 || w < 1 || w > 32) return fail(GRAPHIC_ERR_INVALID_ARG, "R and w must lie in 1..32");
+  if (std::isnan(thresh)) return fail(GRAPHIC_ERR_INVALID_ARG, "thresh is NaN");
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  int rc;
+  if ((rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, register_keys_bytes(T), false))) return rc;
+  if ((rc = begin_call(c))) return rc;
+  RegArgs a;
+  a.in = in;
+  a.out = out;
+  a.iters = iters;
+  a.status = c->d_status;
+  a.T = T;
+  a.n = n;
+  a.thresh = thresh;
+  a.R = R;
+  a.min_size = min_size;
+  a.max_size = max_size;
+  a.w = w;
+  unsigned long long *keys = reinterpret_cast<unsigned long long *>(c->d_scratch);
+  prof_begin(c, GRAPHIC_K_REG_ARGMAX);
+  cudaError_t e = launch_register_argmax(a, keys, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "registration argmax kernel");
+  prof_begin(c, GRAPHIC_K_REG_FIT);
+  e = launch_register_fit(a, keys, c->stream);
+  prof_end(c);
+  if (e != cudaSuccess) return cuda_fail(e, "registration fit kernel");
+  return end_call(c);
+}
+
 int graphic_profile(graphic_ctx *c, int enable) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
   c->prof = enable != 0;
@@ -1701,7 +1738,8 @@ int graphic_profile_read(graphic_ctx *c, double *ms, int64_t *launches, int32_t 
 
 const char *graphic_kernel_name(int32_t k) {
   static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_median", "rot_pass1",
-                                              "rot_pass2", "rot_pass3", "collapse_median", "batch_persistent"};
+                                              "rot_pass2", "rot_pass3", "collapse_median", "batch_persistent",
+                                              "register_argmax", "register_fit"};
   return (k >= 0 && k < GRAPHIC_K_COUNT) ? names[k] : nullptr;
 }
 

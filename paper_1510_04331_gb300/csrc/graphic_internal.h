@@ -183,4 +183,21 @@ cudaError_t launch_bad_mark(float *cube, long long T, int n, const uint8_t *map,
 cudaError_t launch_bad_pass(const float *src, float *dst, long long T, int n, unsigned long long *counts,
                             cudaStream_t st);
 
+// register.cu: registration (Sect. 3.1), one CTA per frame
+struct RegArgs {
+  const float *in;   // T x n x n device
+  double *out;       // T x 8 device: found, x0, y0, fwhm, I0, alpha, beta, Bg
+  int *iters;        // T device: Levenberg-Marquardt iterations made
+  int *status;
+  long long T;
+  int n;
+  double thresh;
+  int R, min_size, max_size, w;
+};
+// keys: device workspace of register_keys_bytes(T), the packed per-frame
+// maximum that the argmax kernel writes (zeroed here) and the fit reads
+size_t register_keys_bytes(long long T);
+cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, cudaStream_t st);
+cudaError_t launch_register_fit(const RegArgs &a, const unsigned long long *keys, cudaStream_t st);
+
 }  // namespace graphic

@@ -1,0 +1,434 @@
+// register.cu -- registration (Sect. 3.1): per frame the centroid of the
+// patch of contiguous pixels above a threshold around the brightest pixel,
+// then a Moffat fit by Levenberg-Marquardt started there; the centre gives
+// the recentring shift, alpha and beta the FWHM.
+//
+// Two kernels.
+//  * frame_argmax_kernel: the only pass over whole frames, HBM-bound.  One
+//    block per (frame, chunk of REG_CHUNK pixels), 16-byte loads; each block
+//    merges its maximum into the frame's 64-bit word by atomicMax on the
+//    packed (total-order key of the value, ~index): the largest value wins,
+//    the smallest index on a tie.  A non-finite value sets the word to all
+//    ones (no finite value packs to it) and the status flag.
+//  * register_fit_kernel: one warp per frame.  The box of half-size R around
+//    the seed and its 8-connected flood fill in shared memory (sweeps until
+//    none changes: the fixpoint is the connected component whatever the
+//    order of the updates), FP64 patch sums, then the fit window in the same
+//    shared buffer and the Levenberg-Marquardt loop.  Every sum is a
+//    butterfly (xor) shuffle reduction, which leaves the bit-identical sum in
+//    every lane (each level adds the same two operands, commuted), so every
+//    lane solves the same damped 6 x 6 system and takes the same decisions:
+//    no broadcast, no block barrier, and several frames per SM keep the FP64
+//    pipe busy.  Start values, damping schedule and stopping rules are those
+//    of the FP64 oracle.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "graphic_internal.h"
+
+namespace graphic {
+namespace {
+
+constexpr int ARG_THREADS = 256;
+constexpr int ARG_VEC = 8;                                   // float4 loads per thread per chunk
+constexpr long long REG_CHUNK = (long long)ARG_THREADS * ARG_VEC * 4;   // pixels per block
+constexpr int FIT_WARPS = 4;                                 // frames per block
+constexpr double REG_PI = 3.14159265358979323846;
+constexpr unsigned long long KEY_NONFINITE = ~0ull;
+
+__device__ __forceinline__ uint32_t order_key(float x) {
+  if (x == 0.0f) x = 0.0f;   // -0 and +0 compare equal: the index decides
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ unsigned long long pack(float v, uint32_t idx) {
+  return ((unsigned long long)order_key(v) << 32) | (unsigned long long)(~idx);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(ARG_THREADS) frame_argmax_kernel(const float *__restrict__ in, long long T,
+                                                                   long long nn, long long chunks,
+                                                                   unsigned long long *keys, int *status) {
+  __shared__ unsigned long long part[ARG_THREADS / 32];
+  __shared__ int part_bad[ARG_THREADS / 32];
+  const long long items = T * chunks;
+  const bool vec = (nn & 3) == 0;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const long long f = it / chunks, c = it - f * chunks;
+    const float *fr = in + f * nn;
+    const long long s = c * REG_CHUNK, e = min(nn, s + REG_CHUNK);
+    float best = -INFINITY;
+    long long bi = -1;
+    bool bad = false;
+    if (vec) {
+      const float4 *f4 = reinterpret_cast<const float4 *>(fr);
+      const long long s4 = s >> 2, e4 = e >> 2;
+      float4 v[ARG_VEC];
+#pragma unroll
+      for (int k = 0; k < ARG_VEC; k++) {
+        const long long j = s4 + threadIdx.x + (long long)k * ARG_THREADS;
+        v[k] = j < e4 ? __ldcs(&f4[j]) : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+      }
+#pragma unroll
+      for (int k = 0; k < ARG_VEC; k++) {
+        const long long j = s4 + threadIdx.x + (long long)k * ARG_THREADS;
+        const float q[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+        if (j < e4) {
+#pragma unroll
+          for (int l = 0; l < 4; l++) {
+            bad |= !(fabsf(q[l]) <= 3.402823466e38f);
+            if (q[l] > best || bi < 0) {
+              best = q[l];
+              bi = 4 * j + l;
+            }
+          }
+        }
+      }
+    } else {
+      for (long long j = s + threadIdx.x; j < e; j += ARG_THREADS) {
+        const float x = fr[j];
+        bad |= !(fabsf(x) <= 3.402823466e38f);
+        if (x > best || bi < 0) {
+          best = x;
+          bi = j;
+        }
+      }
+    }
+    unsigned long long key = bi >= 0 ? pack(best, (uint32_t)bi) : 0ull;
+    key = warp_max_u64(key);
+    const int wbad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+      part[threadIdx.x >> 5] = key;
+      part_bad[threadIdx.x >> 5] = wbad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long k = 0;
+      int b = 0;
+      for (int w = 0; w < ARG_THREADS / 32; w++) {
+        k = part[w] > k ? part[w] : k;
+        b |= part_bad[w];
+      }
+      if (b) {
+        atomicMax(&keys[f], KEY_NONFINITE);
+        atomicOr(status, STATUS_NONFINITE);
+      } else {
+        atomicMax(&keys[f], k);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// Moffat profile (Sect. 3.1) at (x, y) and, with g, its partial derivatives in
+// p = (I0, x0, y0, alpha, beta, Bg).
+__device__ __forceinline__ double moffat(const double *p, double x, double y, double *g) {
+  const double I0 = p[0], al = p[3], be = p[4];
+  const double dx = x - p[1], dy = y - p[2], rho2 = dx * dx + dy * dy;
+  const double u = 1.0 + rho2 / (al * al);
+  const double lu = log(u);
+  const double P = exp(-be * lu);
+  const double A = I0 * (be - 1.0) / (REG_PI * al * al);
+  if (g) {
+    const double Pu = P / u;
+    g[0] = (be - 1.0) / (REG_PI * al * al) * P;
+    g[1] = A * be * Pu * 2.0 * dx / (al * al);
+    g[2] = A * be * Pu * 2.0 * dy / (al * al);
+    g[3] = -2.0 * A / al * P + A * 2.0 * be * rho2 * Pu / (al * al * al);
+    g[4] = I0 / (REG_PI * al * al) * P - A * lu * P;
+    g[5] = 1.0;
+  }
+  return A * P + p[5];
+}
+
+// Damped 6 x 6 solve by Cholesky; false when the matrix is not positive definite.
+__device__ bool chol6(const double *A, const double *b, double *x) {
+  double L[21];   // lower triangle, row i at i (i + 1) / 2
+#pragma unroll
+  for (int i = 0; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) {
+      double s = A[i * 6 + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      if (i == j) {
+        if (!(s > 0)) return false;
+        L[i * (i + 1) / 2 + i] = sqrt(s);
+      } else {
+        L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+      }
+    }
+  double y[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    double s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) s -= L[i * (i + 1) / 2 + k] * y[k];
+    y[i] = s / L[i * (i + 1) / 2 + i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; i--) {
+    double s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; k++) s -= L[k * (k + 1) / 2 + i] * x[k];
+    x[i] = s / L[i * (i + 1) / 2 + i];
+  }
+  return true;
+}
+
+// Squared error of the model p over the window (lane partial, then warp sum).
+__device__ __forceinline__ double window_cost(const double *p, const float *win, int WH, int WW, int wr0, int wc0,
+                                              int lane) {
+  double s = 0.0;
+  for (int i = lane; i < WH * WW; i += 32) {
+    const int r = i / WW, c = i - r * WW;
+    const double e = moffat(p, (double)(c + wc0), (double)(r + wr0), nullptr) - (double)win[i];
+    s += e * e;
+  }
+  return warp_sum(s);
+}
+
+__global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegArgs a,
+                                                                      const unsigned long long *__restrict__ keys,
+                                                                      int side) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long f = (long long)blockIdx.x * FIT_WARPS + wid;
+  if (f >= a.T) return;
+  const int S2 = side * side;
+  float *buf = reinterpret_cast<float *>(smem + (size_t)wid * (((size_t)S2 * 5 + 15) & ~(size_t)15));
+  uint8_t *lab = reinterpret_cast<uint8_t *>(buf + S2);
+  const int n = a.n;
+  const float *fr = a.in + f * (long long)n * n;
+  double *out = a.out + f * 8;
+  const unsigned long long key = keys[f];
+  auto not_found = [&]() {
+    if (lane < 8) out[lane] = 0.0;
+    if (lane == 0 && a.iters) a.iters[f] = 0;
+  };
+  if (key == KEY_NONFINITE) {
+    not_found();
+    return;
+  }
+  const long long seed = (long long)(~(uint32_t)(key & 0xffffffffull));
+  if (key == 0ull || seed >= (long long)a.n * a.n) {   // no maximum recorded: cannot happen for n >= 1
+    if (lane == 0) atomicOr(a.status, STATUS_INTERNAL);
+    not_found();
+    return;
+  }
+  const int r0 = (int)(seed / n), c0 = (int)(seed - (long long)r0 * n), R = a.R;
+  const int rlo = max(r0 - R, 0), rhi = min(r0 + R, n - 1), clo = max(c0 - R, 0), chi = min(c0 + R, n - 1);
+  const int H = rhi - rlo + 1, W = chi - clo + 1;
+  const double th = a.thresh;
+
+  // ---- patch: flood fill of the pixels above the threshold ----------------
+  // lab: 0 below the threshold, 2 above and not (yet) reached, 1 in the patch
+  for (int i = lane; i < H * W; i += 32) {
+    const int r = i / W, c = i - r * W;
+    const float v = fr[(long long)(r + rlo) * n + (c + clo)];
+    buf[i] = v;
+    lab[i] = (double)v > th ? 2 : 0;
+  }
+  __syncwarp();
+  const int si = (r0 - rlo) * W + (c0 - clo);
+  if (lab[si] == 0) {   // the seed itself is not above the threshold
+    not_found();
+    return;
+  }
+  __syncwarp();
+  if (lane == 0) lab[si] = 1;
+  __syncwarp();
+  for (int sweep = 0; sweep <= H * W; sweep++) {
+    bool changed = false;
+    for (int i = lane; i < H * W; i += 32) {
+      if (lab[i] != 2) continue;
+      const int r = i / W, c = i - r * W;
+      bool nb = false;
+      for (int dr = -1; dr <= 1; dr++)
+        for (int dc = -1; dc <= 1; dc++) {
+          const int rr = r + dr, cc = c + dc;
+          if ((dr || dc) && rr >= 0 && rr < H && cc >= 0 && cc < W && lab[rr * W + cc] == 1) nb = true;
+        }
+      if (nb) {
+        lab[i] = 1;
+        changed = true;
+      }
+    }
+    __syncwarp();
+    if (!__any_sync(0xffffffffu, changed)) break;
+  }
+  double cnt = 0.0, sv = 0.0, sx = 0.0, sy = 0.0;
+  bool touch = false;
+  for (int i = lane; i < H * W; i += 32) {
+    if (lab[i] != 1) continue;
+    const int r = i / W, c = i - r * W;
+    const double v = buf[i];
+    cnt += 1.0;
+    sv += v;
+    sx += v * (double)(c + clo);
+    sy += v * (double)(r + rlo);
+    touch |= (r == 0 && rlo > 0) || (r == H - 1 && rhi < n - 1) || (c == 0 && clo > 0) || (c == W - 1 && chi < n - 1);
+  }
+  cnt = warp_sum(cnt);
+  sv = warp_sum(sv);
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  const int size = (int)cnt;
+  if (__any_sync(0xffffffffu, touch) || size < a.min_size || size > a.max_size) {
+    not_found();
+    return;
+  }
+  const double cx = sx / sv, cy = sy / sv;
+
+  // ---- Moffat fit ---------------------------------------------------------
+  const int rc = (int)floor(cy + 0.5), cc = (int)floor(cx + 0.5), w = a.w;
+  const int wr0 = max(rc - w, 0), wr1 = min(rc + w, n - 1), wc0 = max(cc - w, 0), wc1 = min(cc + w, n - 1);
+  const int WH = wr1 - wr0 + 1, WW = wc1 - wc0 + 1;
+  __syncwarp();   // the box reads are done: the buffer now takes the window
+  float lmin = INFINITY;
+  for (int i = lane; i < WH * WW; i += 32) {
+    const int r = i / WW, c = i - r * WW;
+    const float v = fr[(long long)(r + wr0) * n + (c + wc0)];
+    buf[i] = v;
+    lmin = fminf(lmin, v);
+  }
+  __syncwarp();
+  const double bg = warp_min(lmin);
+  double i0 = 0.0;
+  for (int i = lane; i < WH * WW; i += 32) i0 += (double)buf[i] - bg;
+  i0 = warp_sum(i0);
+  double p[6] = {i0, cx, cy, fmax(1.0, sqrt((double)size / REG_PI)), 2.5, bg};
+  double cost = window_cost(p, buf, WH, WW, wr0, wc0, lane);
+  double lambda = 1e-3;
+  int it;
+  for (it = 0; it < 200; it++) {
+    double ne[27];   // J^T J lower triangle (21), J^T r (6)
+#pragma unroll
+    for (int k = 0; k < 27; k++) ne[k] = 0.0;
+    for (int i = lane; i < WH * WW; i += 32) {
+      const int r = i / WW, c = i - r * WW;
+      double g[6];
+      const double e = moffat(p, (double)(c + wc0), (double)(r + wr0), g) - (double)buf[i];
+      int k = 0;
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++)
+#pragma unroll
+        for (int jj = 0; jj <= ii; jj++) ne[k++] += g[ii] * g[jj];
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++) ne[21 + ii] += g[ii] * e;
+    }
+#pragma unroll
+    for (int k = 0; k < 27; k++) ne[k] = warp_sum(ne[k]);
+    bool accepted = false;
+    double newcost = cost;
+    for (int tries = 0; tries < 10; tries++) {
+      double A[36], mg[6], d[6], q[6];
+      int k = 0;
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++)
+#pragma unroll
+        for (int jj = 0; jj <= ii; jj++) {
+          A[ii * 6 + jj] = ne[k];
+          A[jj * 6 + ii] = ne[k];
+          k++;
+        }
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++) {
+        const double di = A[ii * 6 + ii] > 0 ? A[ii * 6 + ii] : 1e-12;
+        A[ii * 6 + ii] += lambda * di;
+        mg[ii] = -ne[21 + ii];
+      }
+      if (!chol6(A, mg, d)) {
+        lambda *= 10.0;
+        continue;
+      }
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++) q[ii] = p[ii] + d[ii];
+      if (!(q[3] > 0) || !(q[4] > 1.0)) {
+        lambda *= 10.0;
+        continue;
+      }
+      newcost = window_cost(q, buf, WH, WW, wr0, wc0, lane);
+      if (newcost < cost) {
+#pragma unroll
+        for (int ii = 0; ii < 6; ii++) p[ii] = q[ii];
+        lambda = fmax(lambda / 10.0, 1e-12);
+        accepted = true;
+        break;
+      }
+      lambda *= 10.0;
+    }
+    if (!accepted) break;
+    const double drop = cost - newcost;
+    cost = newcost;
+    if (drop <= 1e-14 * cost) {
+      it++;
+      break;
+    }
+  }
+  if (lane == 0) {
+    out[0] = 1.0;
+    out[1] = p[1];
+    out[2] = p[2];
+    out[3] = 2.0 * p[3] * sqrt(pow(2.0, 1.0 / p[4]) - 1.0);
+    out[4] = p[0];
+    out[5] = p[3];
+    out[6] = p[4];
+    out[7] = p[5];
+    if (a.iters) a.iters[f] = it;
+  }
+}
+
+}  // namespace
+
+size_t register_keys_bytes(long long T) { return (size_t)T * sizeof(unsigned long long); }
+
+cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, cudaStream_t st) {
+  if (a.T <= 0) return cudaSuccess;
+  const long long nn = (long long)a.n * a.n;
+  cudaError_t e = cudaMemsetAsync(keys, 0, register_keys_bytes(a.T), st);
+  if (e != cudaSuccess) return e;
+  const long long chunks = (nn + REG_CHUNK - 1) / REG_CHUNK;
+  const long long items = a.T * chunks;
+  const unsigned grid = (unsigned)(items < 152LL * 64 ? items : 152LL * 64);
+  frame_argmax_kernel<<<grid, ARG_THREADS, 0, st>>>(a.in, a.T, nn, chunks, keys, a.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_register_fit(const RegArgs &a, const unsigned long long *keys, cudaStream_t st) {
+  if (a.T <= 0) return cudaSuccess;
+  const int side = 2 * (a.R > a.w ? a.R : a.w) + 1;
+  const size_t per_warp = ((size_t)side * side * 5 + 15) & ~(size_t)15;
+  const size_t smem = per_warp * FIT_WARPS;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(register_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long long blocks = (a.T + FIT_WARPS - 1) / FIT_WARPS;
+  register_fit_kernel<<<(unsigned)blocks, FIT_WARPS * 32, smem, st>>>(a, keys, side);
+  return cudaGetLastError();
+}
+
+}  // namespace graphic

@@ -31,7 +31,7 @@ ERRORS = {
     -7: "GRAPHIC_ERR_INTERNAL",
 }
 KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median",
-           "batch_persistent"]
+           "batch_persistent", "register_argmax", "register_fit"]
 BATCH_PER_CUBE = 0
 BATCH_PERSISTENT = 1
 BATCH_GROUPED = 2
@@ -119,6 +119,7 @@ _SIGS = {
     "graphic_sky_subtract": [_P, _P, _P, _I64, _I32, _P, _I32, _D, _D],
     "graphic_bad_pixel_map": [_P, _P, _I32, ctypes.c_double, _P],
     "graphic_bad_pixel_fix": [_P, _P, _I64, _I32, _P],
+    "graphic_register": [_P, _P, _I64, _I32, ctypes.c_double, _I32, _I32, _I32, _I32, _P, _P],
     "graphic_reduce_host": [_P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
     "graphic_profile": [_P, ctypes.c_int],
     "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
@@ -398,6 +399,22 @@ class Context:
                                            None if bad_map is None else _P(bad_map.data_ptr())))
         return cube
 
+    def graphic_register(self, cube, thresh, R, min_size, max_size, w, out=None, iters=None):
+        """Per frame: centroid of the thresholded patch around the brightest
+        pixel, then a Moffat fit (Levenberg-Marquardt) started there.  Returns
+        a (T, 8) float64 CUDA tensor: found, x0, y0, FWHM, I0, alpha, beta, Bg
+        (iters, if given, a (T,) int32 CUDA tensor, receives the iterations)."""
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        if out is None:
+            out = torch.empty((T, 8), dtype=torch.float64, device=cube.device)
+        self._stream()
+        _check(lib().graphic_register(self.h, _P(cube.data_ptr()), T, n, float(thresh), int(R), int(min_size),
+                                      int(max_size), int(w), _P(out.data_ptr()),
+                                      None if iters is None else _P(iters.data_ptr())))
+        return out
+
     def set_precision(self, precision: int):
         """PREC_FP32 (default), PREC_BF16X3 or PREC_FP16X3: arithmetic of the
         line passes for frames of n = 1024 (tensor-core DFT stages)."""
@@ -559,3 +576,7 @@ def graphic_rotate_noalloc(cube, theta_deg, out):
 
 def graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, device=0, out_host=None):
     return context(device).graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, out_host)
+
+
+def graphic_register(cube, thresh, R, min_size, max_size, w, out=None, iters=None):
+    return context().graphic_register(cube, thresh, R, min_size, max_size, w, out, iters)

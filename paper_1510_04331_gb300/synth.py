@@ -229,3 +229,47 @@ def uneven_batch(seed: int = 3, n_cubes: int = 48, sides=(64, 128, 256, 512, 102
         cube += (100.0 * np.exp(-((xx - n / 2) ** 2 + (yy - n / 2) ** 2) / (2 * 1.7 ** 2))).astype(np.float32)
         out.append((cube, dx, dy, th))
     return out
+
+
+@dataclass
+class StarFrames:
+    cube: np.ndarray          # float32 [T][N][N], sky-subtracted raw frames
+    x: np.ndarray             # float64 [T], true star centre (column), NaN where the star is lost
+    y: np.ndarray             # float64 [T], true star centre (row)
+    fwhm: float               # FWHM of the core Gaussian, px
+    peak: float
+
+
+def star_frames(T: int, N: int, seed: int, *, fwhm: float = 4.0, peak: float = 1e4, jitter: float = 20.0,
+                halo=((2.0, 0.08), (4.5, 0.012)), sky: float = 50.0, read: float = 5.0, lost: float = 0.0,
+                second: float = 0.0) -> StarFrames:
+    """Raw frames for registration: a star at (N/2, N/2) + delta, delta ~
+    U(-jitter, jitter) px per axis (dithering and tip-tilt jitter), whose
+    profile is a Gaussian core of FWHM ``fwhm`` and peak ``peak`` plus halo
+    Gaussians of ``halo`` = (width factor, relative peak) pairs (a wing
+    heavier than the core, as an AO-corrected PSF), sky-subtracted with
+    noise N(0, read^2 + image + sky) (the Gaussian limit of the Poisson
+    draw).  A fraction ``lost`` of the frames has the star at 1 % of its peak
+    (AO loss: no patch above a threshold set for good frames).  ``second`` >
+    0 adds a fainter star of that relative peak at a fixed offset (the
+    brightest pixel stays on the target)."""
+    rng = np.random.default_rng(seed)
+    sig = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    cube = np.zeros((T, N, N), np.float32)
+    xs = N / 2.0 + rng.uniform(-jitter, jitter, T)
+    ys = N / 2.0 + rng.uniform(-jitter, jitter, T)
+    is_lost = rng.random(T) < lost
+    half = int(math.ceil(8.0 * sig * max([1.0] + [h[0] for h in halo])))
+    for t in range(T):
+        amp = peak * (0.01 if is_lost[t] else 1.0)
+        frame = np.zeros((N, N), np.float64)
+        _gauss_add(frame, xs[t], ys[t], sig, amp, half)
+        for (k, rel) in halo:
+            _gauss_add(frame, xs[t], ys[t], k * sig, amp * rel, half)
+        if second > 0:
+            _gauss_add(frame, xs[t] + 0.3 * N / 2, ys[t] - 0.2 * N / 2, sig, amp * second, half)
+        var = read * read + sky + np.maximum(frame, 0.0)
+        cube[t] = (frame + np.sqrt(var) * rng.standard_normal((N, N))).astype(np.float32)
+    x = np.where(is_lost, np.nan, xs)
+    y = np.where(is_lost, np.nan, ys)
+    return StarFrames(cube=cube, x=x, y=y, fwhm=fwhm, peak=peak)
