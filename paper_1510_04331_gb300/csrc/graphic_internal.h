@@ -194,10 +194,11 @@ struct RegArgs {
   double thresh;
   int R, min_size, max_size, w;
 };
-// keys: device workspace of register_keys_bytes(T), the packed per-frame
-// maximum that the argmax kernel writes (zeroed here) and the fit reads
+// keys: device workspace of register_keys_bytes(T): the packed per-frame
+// maxima that the argmax kernel writes and the fit reads, then the fit's
+// frame counter (all zeroed by launch_register_argmax)
 size_t register_keys_bytes(long long T);
 cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, cudaStream_t st);
-cudaError_t launch_register_fit(const RegArgs &a, const unsigned long long *keys, cudaStream_t st);
+cudaError_t launch_register_fit(const RegArgs &a, unsigned long long *keys, cudaStream_t st);
 
 }  // namespace graphic

@@ -33,7 +33,7 @@ namespace {
 constexpr int ARG_THREADS = 256;
 constexpr int ARG_VEC = 8;                                   // float4 loads per thread per chunk
 constexpr long long REG_CHUNK = (long long)ARG_THREADS * ARG_VEC * 4;   // pixels per block
-constexpr int FIT_WARPS = 4;                                 // frames per block
+constexpr int FIT_WARPS = 1;   // one warp (frame) per block: small batches spread over all SMs
 constexpr double REG_PI = 3.14159265358979323846;
 constexpr unsigned long long KEY_NONFINITE = ~0ull;
 
@@ -142,25 +142,27 @@ __device__ __forceinline__ float warp_min(float x) {
   return x;
 }
 
-// Moffat profile (Sect. 3.1) at (x, y) and, with g, its partial derivatives in
-// p = (I0, x0, y0, alpha, beta, Bg).
-__device__ __forceinline__ double moffat(const double *p, double x, double y, double *g) {
+// Moffat profile (Sect. 3.1) with parameters p = (I0, x0, y0, alpha, beta,
+// Bg): the quotients that do not depend on the pixel, once per parameter set.
+struct MoffatConst {
+  double x0, y0, beta, bg, ia2, A, c0, c1, c3, c4, c5;
+};
+
+__device__ __forceinline__ MoffatConst moffat_const(const double *p) {
+  MoffatConst k;
   const double I0 = p[0], al = p[3], be = p[4];
-  const double dx = x - p[1], dy = y - p[2], rho2 = dx * dx + dy * dy;
-  const double u = 1.0 + rho2 / (al * al);
-  const double lu = log(u);
-  const double P = exp(-be * lu);
-  const double A = I0 * (be - 1.0) / (REG_PI * al * al);
-  if (g) {
-    const double Pu = P / u;
-    g[0] = (be - 1.0) / (REG_PI * al * al) * P;
-    g[1] = A * be * Pu * 2.0 * dx / (al * al);
-    g[2] = A * be * Pu * 2.0 * dy / (al * al);
-    g[3] = -2.0 * A / al * P + A * 2.0 * be * rho2 * Pu / (al * al * al);
-    g[4] = I0 / (REG_PI * al * al) * P - A * lu * P;
-    g[5] = 1.0;
-  }
-  return A * P + p[5];
+  k.x0 = p[1];
+  k.y0 = p[2];
+  k.beta = be;
+  k.bg = p[5];
+  k.ia2 = 1.0 / (al * al);
+  k.A = I0 * (be - 1.0) * k.ia2 / REG_PI;      // I0 (beta - 1) / (pi alpha^2)
+  k.c0 = (be - 1.0) * k.ia2 / REG_PI;          // dI/dI0 = c0 P
+  k.c1 = 2.0 * k.A * be * k.ia2;               // dI/dx0 = c1 P / u dx
+  k.c3 = -2.0 * k.A / al;                      // dI/dalpha = c3 P + c4 rho^2 P / u
+  k.c4 = k.c1 / al;
+  k.c5 = I0 * k.ia2 / REG_PI;                  // dI/dbeta = c5 P - A ln(u) P
+  return k;
 }
 
 // Damped 6 x 6 solve by Cholesky; false when the matrix is not positive definite.
@@ -198,32 +200,53 @@ __device__ bool chol6(const double *A, const double *b, double *x) {
   return true;
 }
 
-// Squared error of the model p over the window (lane partial, then warp sum).
-__device__ __forceinline__ double window_cost(const double *p, const float *win, int WH, int WW, int wr0, int wc0,
-                                              int lane) {
-  double s = 0.0;
+// One pass over the window at the parameters k: the squared error of the
+// model and the normal equations of its analytic Jacobian (J^T J lower
+// triangle in ne[0..21), J^T r in ne[21..27)), lane partials then warp sums
+// (every lane ends with the same values).  The oracle takes the two in
+// separate passes; one pass serves both here because the normal equations
+// of an accepted trial point are those of the next iteration.
+__device__ __forceinline__ double window_pass(const MoffatConst &k, const float *win, int WH, int WW, int wr0,
+                                              int wc0, int lane, double *ne) {
+  double cost = 0.0;
+#pragma unroll
+  for (int q = 0; q < 27; q++) ne[q] = 0.0;
   for (int i = lane; i < WH * WW; i += 32) {
     const int r = i / WW, c = i - r * WW;
-    const double e = moffat(p, (double)(c + wc0), (double)(r + wr0), nullptr) - (double)win[i];
-    s += e * e;
+    const double dx = (double)(c + wc0) - k.x0, dy = (double)(r + wr0) - k.y0;
+    const double rho2 = dx * dx + dy * dy;
+    const double u = 1.0 + rho2 * k.ia2;
+    const double lu = log(u);
+    const double P = exp(-k.beta * lu);
+    const double Pu = P / u;
+    const double e = k.A * P + k.bg - (double)win[i];
+    double g[6];
+    g[0] = k.c0 * P;
+    g[1] = k.c1 * Pu * dx;
+    g[2] = k.c1 * Pu * dy;
+    g[3] = k.c3 * P + k.c4 * rho2 * Pu;
+    g[4] = k.c5 * P - k.A * lu * P;
+    g[5] = 1.0;
+    cost += e * e;
+    int q = 0;
+#pragma unroll
+    for (int ii = 0; ii < 6; ii++)
+#pragma unroll
+      for (int jj = 0; jj <= ii; jj++) ne[q++] += g[ii] * g[jj];
+#pragma unroll
+    for (int ii = 0; ii < 6; ii++) ne[21 + ii] += g[ii] * e;
   }
-  return warp_sum(s);
+#pragma unroll
+  for (int q = 0; q < 27; q++) ne[q] = warp_sum(ne[q]);
+  return warp_sum(cost);
 }
 
-__global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegArgs a,
-                                                                      const unsigned long long *__restrict__ keys,
-                                                                      int side) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long f = (long long)blockIdx.x * FIT_WARPS + wid;
-  if (f >= a.T) return;
-  const int S2 = side * side;
-  float *buf = reinterpret_cast<float *>(smem + (size_t)wid * (((size_t)S2 * 5 + 15) & ~(size_t)15));
-  uint8_t *lab = reinterpret_cast<uint8_t *>(buf + S2);
+// One frame on one warp: seed from the argmax word, patch, centroid, fit.
+__device__ __forceinline__ void fit_frame(const RegArgs &a, unsigned long long key, long long f, float *buf,
+                                          uint8_t *lab, double *ne_cur, int lane) {
   const int n = a.n;
   const float *fr = a.in + f * (long long)n * n;
   double *out = a.out + f * 8;
-  const unsigned long long key = keys[f];
   auto not_found = [&]() {
     if (lane < 8) out[lane] = 0.0;
     if (lane == 0 && a.iters) a.iters[f] = 0;
@@ -233,7 +256,7 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
     return;
   }
   const long long seed = (long long)(~(uint32_t)(key & 0xffffffffull));
-  if (key == 0ull || seed >= (long long)a.n * a.n) {   // no maximum recorded: cannot happen for n >= 1
+  if (key == 0ull || seed >= (long long)n * n) {   // no maximum recorded: cannot happen for n >= 1
     if (lane == 0) atomicOr(a.status, STATUS_INTERNAL);
     not_found();
     return;
@@ -245,6 +268,7 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
 
   // ---- patch: flood fill of the pixels above the threshold ----------------
   // lab: 0 below the threshold, 2 above and not (yet) reached, 1 in the patch
+  __syncwarp();   // the previous frame's reads of buf and lab are done
   for (int i = lane; i < H * W; i += 32) {
     const int r = i / W, c = i - r * W;
     const float v = fr[(long long)(r + rlo) * n + (c + clo)];
@@ -320,27 +344,16 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
   for (int i = lane; i < WH * WW; i += 32) i0 += (double)buf[i] - bg;
   i0 = warp_sum(i0);
   double p[6] = {i0, cx, cy, fmax(1.0, sqrt((double)size / REG_PI)), 2.5, bg};
-  double cost = window_cost(p, buf, WH, WW, wr0, wc0, lane);
+  double ne[27];
+  double cost = window_pass(moffat_const(p), buf, WH, WW, wr0, wc0, lane, ne);
+  // ne_cur: the normal equations at p (identical in every lane: lane q keeps q)
+#pragma unroll
+  for (int q = 0; q < 27; q++)
+    if (lane == q) ne_cur[q] = ne[q];
+  __syncwarp();
   double lambda = 1e-3;
   int it;
   for (it = 0; it < 200; it++) {
-    double ne[27];   // J^T J lower triangle (21), J^T r (6)
-#pragma unroll
-    for (int k = 0; k < 27; k++) ne[k] = 0.0;
-    for (int i = lane; i < WH * WW; i += 32) {
-      const int r = i / WW, c = i - r * WW;
-      double g[6];
-      const double e = moffat(p, (double)(c + wc0), (double)(r + wr0), g) - (double)buf[i];
-      int k = 0;
-#pragma unroll
-      for (int ii = 0; ii < 6; ii++)
-#pragma unroll
-        for (int jj = 0; jj <= ii; jj++) ne[k++] += g[ii] * g[jj];
-#pragma unroll
-      for (int ii = 0; ii < 6; ii++) ne[21 + ii] += g[ii] * e;
-    }
-#pragma unroll
-    for (int k = 0; k < 27; k++) ne[k] = warp_sum(ne[k]);
     bool accepted = false;
     double newcost = cost;
     for (int tries = 0; tries < 10; tries++) {
@@ -350,15 +363,15 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
       for (int ii = 0; ii < 6; ii++)
 #pragma unroll
         for (int jj = 0; jj <= ii; jj++) {
-          A[ii * 6 + jj] = ne[k];
-          A[jj * 6 + ii] = ne[k];
+          A[ii * 6 + jj] = ne_cur[k];
+          A[jj * 6 + ii] = ne_cur[k];
           k++;
         }
 #pragma unroll
       for (int ii = 0; ii < 6; ii++) {
         const double di = A[ii * 6 + ii] > 0 ? A[ii * 6 + ii] : 1e-12;
         A[ii * 6 + ii] += lambda * di;
-        mg[ii] = -ne[21 + ii];
+        mg[ii] = -ne_cur[21 + ii];
       }
       if (!chol6(A, mg, d)) {
         lambda *= 10.0;
@@ -370,10 +383,15 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
         lambda *= 10.0;
         continue;
       }
-      newcost = window_cost(q, buf, WH, WW, wr0, wc0, lane);
+      newcost = window_pass(moffat_const(q), buf, WH, WW, wr0, wc0, lane, ne);
       if (newcost < cost) {
 #pragma unroll
         for (int ii = 0; ii < 6; ii++) p[ii] = q[ii];
+        __syncwarp();   // every lane has read ne_cur
+#pragma unroll
+        for (int qq = 0; qq < 27; qq++)
+          if (lane == qq) ne_cur[qq] = ne[qq];
+        __syncwarp();
         lambda = fmax(lambda / 10.0, 1e-12);
         accepted = true;
         break;
@@ -401,9 +419,32 @@ __global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegA
   }
 }
 
+// Persistent warps: each takes the next frame from the counter after the
+// per-frame words (no waiting on other warps).
+__global__ void __launch_bounds__(FIT_WARPS * 32) register_fit_kernel(const RegArgs a,
+                                                                      unsigned long long *__restrict__ keys,
+                                                                      int side) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int S2 = side * side;
+  const size_t per_warp = (((size_t)S2 * 5 + 15) & ~(size_t)15) + 27 * sizeof(double);
+  unsigned char *base = smem + (size_t)wid * per_warp;
+  float *buf = reinterpret_cast<float *>(base);
+  uint8_t *lab = reinterpret_cast<uint8_t *>(buf + S2);
+  double *ne_cur = reinterpret_cast<double *>(base + (((size_t)S2 * 5 + 15) & ~(size_t)15));
+  unsigned long long *counter = keys + a.T;
+  for (;;) {
+    long long f = 0;
+    if (lane == 0) f = (long long)atomicAdd(counter, 1ull);
+    f = __shfl_sync(0xffffffffu, f, 0);
+    if (f >= a.T) break;
+    fit_frame(a, keys[f], f, buf, lab, ne_cur, lane);
+  }
+}
+
 }  // namespace
 
-size_t register_keys_bytes(long long T) { return (size_t)T * sizeof(unsigned long long); }
+size_t register_keys_bytes(long long T) { return (size_t)(T + 1) * sizeof(unsigned long long); }
 
 cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, cudaStream_t st) {
   if (a.T <= 0) return cudaSuccess;
@@ -417,17 +458,23 @@ cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_register_fit(const RegArgs &a, const unsigned long long *keys, cudaStream_t st) {
+cudaError_t launch_register_fit(const RegArgs &a, unsigned long long *keys, cudaStream_t st) {
   if (a.T <= 0) return cudaSuccess;
   const int side = 2 * (a.R > a.w ? a.R : a.w) + 1;
-  const size_t per_warp = ((size_t)side * side * 5 + 15) & ~(size_t)15;
+  const size_t per_warp = (((size_t)side * side * 5 + 15) & ~(size_t)15) + 27 * sizeof(double);
   const size_t smem = per_warp * FIT_WARPS;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(register_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const long long blocks = (a.T + FIT_WARPS - 1) / FIT_WARPS;
-  register_fit_kernel<<<(unsigned)blocks, FIT_WARPS * 32, smem, st>>>(a, keys, side);
+  cudaError_t e = cudaFuncSetAttribute(register_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, register_fit_kernel, FIT_WARPS * 32, smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long need = (a.T + FIT_WARPS - 1) / FIT_WARPS;
+  long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+  if (grid > need) grid = need;
+  register_fit_kernel<<<(unsigned)grid, FIT_WARPS * 32, smem, st>>>(a, keys, side);
   return cudaGetLastError();
 }
 
