@@ -101,6 +101,10 @@ def _load():
                                                   ctypes.c_double, ctypes.c_int, _d]
             lib.oracle_moffat_fwhm.argtypes = [ctypes.c_double, ctypes.c_double]
             lib.oracle_moffat_fwhm.restype = ctypes.c_double
+            lib.oracle_bin_median_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _f]
+            lib.oracle_inject_f32.argtypes = [_f, ctypes.c_longlong, ctypes.c_int, _d, _d, _d, ctypes.c_int, _d, _d,
+                                              _d, _d, _d, ctypes.c_int]
+            lib.oracle_aperture_f32.argtypes = [_f, ctypes.c_int, ctypes.c_int, _d, _d, ctypes.c_double, _d]
             lib.oracle_last_max_imag.restype = ctypes.c_double
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -385,3 +389,45 @@ def register(cube, thresh: float, R: int, min_size: int, max_size: int, w: int):
         found[t] = True
         x0[t], y0[t], fw[t] = p[1], p[2], moffat_fwhm(p[3], p[4])
     return found, x0, y0, fw
+
+
+# --------------------------------------------------------------------------
+# Photometric-accuracy and binning experiments (Sect. 4.2, 4.3)
+# --------------------------------------------------------------------------
+
+def bin_median(cube, B: int) -> np.ndarray:
+    """Per-pixel median of each group of B consecutive frames (the last group
+    may be shorter): ceil(T / B) frames."""
+    c = _f32(cube)
+    T, N = c.shape[0], c.shape[1]
+    out = np.empty(((T + B - 1) // B, N, N), np.float32)
+    if _load().oracle_bin_median_f32(_p(c, _f), T, N, int(B), _p(out, _f)) != 0:
+        raise ValueError("bad arguments")
+    return out
+
+
+def inject(cube, parang, xc, yc, r, pa0, flux, alpha, beta, half: int) -> np.ndarray:
+    """A copy of cube with Moffat companions (radius r_j, position angle
+    pa0_j + parang_t, total flux flux_j, per-frame alpha, beta) added around
+    the per-frame centres (xc, yc) on windows of half-size `half`."""
+    c = _f32(cube).copy()
+    T, N = c.shape[0], c.shape[1]
+    pa, x, y = (_c64(np.broadcast_to(np.asarray(v, np.float64), (T,))) for v in (parang, xc, yc))
+    al, be = (_c64(np.broadcast_to(np.asarray(v, np.float64), (T,))) for v in (alpha, beta))
+    r, pa0, flux = (_c64(np.atleast_1d(v)) for v in (r, pa0, flux))
+    if _load().oracle_inject_f32(_p(c, _f), T, N, _p(pa, _d), _p(x, _d), _p(y, _d), len(r), _p(r, _d), _p(pa0, _d),
+                                 _p(flux, _d), _p(al, _d), _p(be, _d), int(half)) != 0:
+        raise ValueError("bad arguments")
+    return c
+
+
+def aperture(img, x, y, radius: float) -> np.ndarray:
+    """FP64 sums of img over the pixels within `radius` of each (x, y)."""
+    f = _f32(img)
+    x, y = _c64(np.atleast_1d(x)), _c64(np.atleast_1d(y))
+    out = np.zeros(len(x))
+    if _load().oracle_aperture_f32(_p(f, _f), f.shape[0], len(x), _p(x, _d), _p(y, _d), float(radius),
+                                   _p(out, _d)) != 0:
+        raise ValueError("bad arguments")
+    return out
+

@@ -938,3 +938,89 @@ double oracle_moffat_fwhm(double alpha, double beta)
 {
     return 2.0 * alpha * sqrt(pow(2.0, 1.0 / beta) - 1.0);
 }
+
+/* ---------------------------------------------------------------------- */
+/* Photometric-accuracy and binning experiments (Sect. 4.2, 4.3)           */
+/* ---------------------------------------------------------------------- */
+
+/* Exported: median binning (Sect. 4.3, "combining each set of ten ... frames
+ * into a single median frame"; the quick-look binning of Sect. 3.1): group g
+ * holds frames [g B, min(T, (g + 1) B)) (the last group may be shorter) and
+ * out[g](p) is the median of its values at pixel p, by the median rule of
+ * the collapse (sort, middle value, mean of the two middle values in FP32
+ * for an even count).  out has ceil(T / B) frames. */
+int oracle_bin_median_f32(const float *cube, long long T, int N, int B, float *out)
+{
+    if (T < 0 || N < 1 || B < 1) return -1;
+    long long G = (T + B - 1) / B, NN = (long long)N * N;
+#pragma omp parallel for schedule(static)
+    for (long long q = 0; q < G * NN; q++) {
+        long long g = q / NN, p = q % NN;
+        long long f0 = g * B, f1 = f0 + B < T ? f0 + B : T;
+        float v[4096];
+        float *buf = (f1 - f0) <= 4096 ? v : (float *)malloc(sizeof(float) * (size_t)(f1 - f0));
+        for (long long f = f0; f < f1; f++) buf[f - f0] = cube[f * NN + p];
+        out[g * NN + p] = median32(buf, f1 - f0);
+        if (buf != v) free(buf);
+    }
+    return 0;
+}
+
+/* Exported: fake companion injection (Sect. 4.2: companions injected into
+ * the raw frames at an angle following the field rotation).  Companion j of
+ * frame t sits at (xc[t] + r_j cos(pa0_j + parang_t), yc[t] + r_j sin(pa0_j +
+ * parang_t)) (x = column, y = row, degrees, counter-clockwise from +x), its
+ * profile the Moffat function of Sect. 3.1 with total flux flux_j and the
+ * frame's alpha[t], beta[t]: flux_j (beta - 1) / (pi alpha^2) (1 + rho^2 /
+ * alpha^2)^(-beta), evaluated in FP64 on the pixels of the square window of
+ * half-size `half` around the rounded position (clipped to the frame) and
+ * added to the FP32 frame as (float)((double)v + sum of the companions). */
+int oracle_inject_f32(float *cube, long long T, int N, const double *parang, const double *xc, const double *yc,
+                      int n_comp, const double *r, const double *pa0, const double *flux, const double *alpha,
+                      const double *beta, int half)
+{
+    if (T < 0 || N < 1 || n_comp < 0 || half < 0) return -1;
+    long long NN = (long long)N * N;
+#pragma omp parallel for schedule(static)
+    for (long long t = 0; t < T; t++) {
+        double *add = (double *)calloc((size_t)NN, sizeof(double));
+        for (int j = 0; j < n_comp; j++) {
+            double ang = (pa0[j] + parang[t]) * ORACLE_PI / 180.0;
+            double xp = xc[t] + r[j] * cos(ang), yp = yc[t] + r[j] * sin(ang);
+            long long cr = (long long)floor(yp + 0.5), cc = (long long)floor(xp + 0.5);
+            double al = alpha[t], be = beta[t];
+            double A = flux[j] * (be - 1.0) / (ORACLE_PI * al * al);
+            for (long long row = cr - half; row <= cr + half; row++) {
+                if (row < 0 || row >= N) continue;
+                for (long long col = cc - half; col <= cc + half; col++) {
+                    if (col < 0 || col >= N) continue;
+                    double dx = (double)col - xp, dy = (double)row - yp;
+                    add[row * N + col] += A * pow(1.0 + (dx * dx + dy * dy) / (al * al), -be);
+                }
+            }
+        }
+        for (long long p = 0; p < NN; p++)
+            if (add[p] != 0.0) cube[t * NN + p] = (float)((double)cube[t * NN + p] + add[p]);
+        free(add);
+    }
+    return 0;
+}
+
+/* Exported: aperture photometry for the recovered flux (Sect. 4.2): out[k]
+ * = sum of img over the pixels whose centres lie within `radius` of (x[k],
+ * y[k]), (col - x)^2 + (row - y)^2 <= radius^2, in FP64. */
+int oracle_aperture_f32(const float *img, int N, int n_ap, const double *x, const double *y, double radius,
+                        double *out)
+{
+    if (N < 1 || n_ap < 0 || !(radius >= 0)) return -1;
+    for (int k = 0; k < n_ap; k++) {
+        double s = 0.0;
+        for (int row = 0; row < N; row++)
+            for (int col = 0; col < N; col++) {
+                double dx = (double)col - x[k], dy = (double)row - y[k];
+                if (dx * dx + dy * dy <= radius * radius) s += (double)img[(size_t)row * N + col];
+            }
+        out[k] = s;
+    }
+    return 0;
+}

@@ -591,3 +591,75 @@ def test_centroid_of_a_symmetric_patch_and_its_flags():
     assert not oracle.centroid(f, 1.0, 5, 6, 10)[0]           # patch too small
     assert not oracle.centroid(f, 1.0, 5, 1, 4)[0]            # patch too large
     assert not oracle.centroid(f, 1.0, 0, 1, 10)[0]           # patch reaches the box edge
+
+
+# --------------------------------------------------------------------------
+# Photometric-accuracy and binning experiments (Sect. 4.2, 4.3)
+# --------------------------------------------------------------------------
+
+def test_bin_median_is_numpy_median_per_group():
+    """Groups of B consecutive frames with a ragged last group; B = 1 is the
+    identity and B >= T the median collapse."""
+    rng = np.random.default_rng(60)
+    c = rng.standard_normal((23, 12, 12)).astype(np.float32)
+    c[3, 2, 2] = c[4, 2, 2]                                        # a tie
+    for B in (1, 2, 5, 10, 23, 40):
+        got = oracle.bin_median(c, B)
+        want = np.stack([np.median(c[g:g + B], axis=0) for g in range(0, 23, B)]).astype(np.float32)
+        assert got.shape == (-(-23 // B), 12, 12)
+        assert np.array_equal(got, want), B
+    assert np.array_equal(oracle.bin_median(c, 1), c)
+    assert np.array_equal(oracle.bin_median(c, 23)[0], oracle.collapse_median(c))
+
+
+def test_inject_total_flux_peak_and_position():
+    """The Moffat companion carries its total flux (the tail outside a
+    square window of half-size H is below (1 + H^2/alpha^2)^(1-beta)), its
+    peak is flux (beta - 1) / (pi alpha^2) at an integer position, and its
+    centre of light is the requested position at radius r, angle pa0 +
+    parang counter-clockwise from +x."""
+    N, H = 256, 120
+    al, be, F = 3.0, 2.5, 5000.0
+    z = np.zeros((1, N, N), np.float32)
+    a = oracle.inject(z, [0.0], [128.0], [128.0], [0.0], [0.0], [F], [al], [be], H)
+    tail = (1.0 + H * H / (al * al)) ** (1.0 - be)
+    assert abs(float(a.astype(np.float64).sum()) - F) <= F * (tail + 1e-5)
+    assert a[0, 128, 128] == np.float32(F * (be - 1.0) / (math.pi * al * al))
+    # 30 deg of parallactic angle + 60 deg of position angle = straight up (+y, higher rows)
+    b = oracle.inject(z, [30.0], [128.0], [128.0], [40.0], [60.0], [F], [al], [be], 60)
+    assert np.unravel_index(np.argmax(b[0]), (N, N)) == (168, 128)
+    # a sub-pixel position: the centre of light follows it
+    th = math.radians(17.0 + 25.0)
+    xp, yp = 128.0 + 33.3 * math.cos(th), 128.0 + 33.3 * math.sin(th)
+    c = oracle.inject(z, [17.0], [128.0], [128.0], [33.3], [25.0], [F], [al], [be], 100).astype(np.float64)[0]
+    yy, xx = np.mgrid[0:N, 0:N]
+    assert abs((c * xx).sum() / c.sum() - xp) < 2e-3 and abs((c * yy).sum() / c.sum() - yp) < 2e-3
+
+
+def test_inject_adds_in_fp64_then_rounds_and_clips_at_the_edges():
+    rng = np.random.default_rng(61)
+    base = rng.normal(100.0, 5.0, (3, 64, 64)).astype(np.float32)
+    kw = dict(parang=[0.0, 10.0, 20.0], xc=[32.0, 31.5, 2.0], yc=[32.0, 30.0, 61.0], r=[5.0, 20.0],
+              pa0=[0.0, 200.0], flux=[800.0, 50.0], alpha=[2.0, 2.5, 3.0], beta=[2.0, 3.0, 4.0], half=12)
+    only = oracle.inject(np.zeros_like(base), **kw).astype(np.float64)
+    both = oracle.inject(base, **kw).astype(np.float64)
+    # one rounding of the FP64 sum: within an ulp of base + (the FP32-rounded injection)
+    ulp = np.spacing(np.abs(base + only).astype(np.float32)).astype(np.float64)
+    assert (np.abs(both - (base.astype(np.float64) + only)) <= ulp + np.spacing(only.astype(np.float32))).all()
+    assert np.array_equal(both[only == 0.0], base.astype(np.float64)[only == 0.0])
+    # frame 2's star sits 2 px from the left edge and 3 from the top: windows clip, nothing wraps
+    assert only[2, :, 40:].sum() == 0.0 and np.isfinite(only).all()
+
+
+def test_aperture_counts_lattice_points_and_sums():
+    """A constant image gives the number of pixel centres in the disc (brute
+    force); a ramp symmetric about an integer centre gives count x value."""
+    N = 64
+    ones = np.ones((N, N), np.float32)
+    yy, xx = np.mgrid[0:N, 0:N]
+    for (x, y, r) in [(32.0, 32.0, 5.0), (10.3, 40.7, 7.5), (0.0, 0.0, 3.0), (31.5, 31.5, 0.0)]:
+        want = float(((xx - x) ** 2 + (yy - y) ** 2 <= r * r).sum())
+        assert oracle.aperture(ones, [x], [y], r)[0] == want
+    ramp = (xx + 2 * yy).astype(np.float32)
+    cnt = float(((xx - 20) ** 2 + (yy - 30) ** 2 <= 36).sum())
+    assert oracle.aperture(ramp, [20.0], [30.0], 6.0)[0] == cnt * (20 + 60)
