@@ -263,6 +263,53 @@ int graphic_bad_pixel_fix(graphic_ctx *ctx, float *cube, int64_t n_frames, int32
 int graphic_register(graphic_ctx *ctx, const float *in, int64_t n_frames, int32_t n, double thresh, int32_t R,
                      int32_t min_size, int32_t max_size, int32_t w, double *out, int32_t *iters);
 
+/* ---- photometric-accuracy and binning experiments (Sect. 4.2, 4.3) ----- */
+
+/*
+ * Median binning (Sect. 4.3: every B consecutive frames combined into one
+ * median frame; the quick-look binning of Sect. 3.1): out[g](p) = median of
+ * in[f](p) over the frames f of group g = [g B, min(n_frames, (g + 1) B)),
+ * the last group possibly shorter, by the median rule of
+ * graphic_collapse_median.  in: device n_frames x n x n; out: device
+ * ceil(n_frames / B) x n x n (16-byte aligned, n as for the reduction).
+ * B >= 1.  GRAPHIC_ERR_NONFINITE on a non-finite value.  Synchronous.
+ */
+int graphic_bin_median(graphic_ctx *ctx, const float *in, float *out, int64_t n_frames, int32_t n, int32_t B);
+
+/*
+ * Host helper for binned sequences: out[g] = mean of v over group g (FP64,
+ * in order), e.g. the parallactic angle or time of a median bin (the paper
+ * does not say which value a bin takes; its mean).  out: ceil(n / B).
+ */
+int graphic_bin_mean(const double *v, int64_t n, int32_t B, double *out);
+
+/*
+ * Fake companion injection (Sect. 4.2: companions added to the raw frames
+ * at an angle that follows the field rotation), in place.  Companion j of
+ * frame t sits at (xc[t] + r[j] cos(pa0[j] + parang[t]), yc[t] + r[j]
+ * sin(pa0[j] + parang[t])) (x = column, y = row, degrees counter-clockwise
+ * from +x; positions in FP64 on the host) with the Moffat profile of
+ * Sect. 3.1, total flux flux[j] and the frame's alpha[t], beta[t]:
+ * flux (beta - 1) / (pi alpha^2) (1 + rho^2 / alpha^2)^(-beta), evaluated in
+ * FP32 on the square window of half-size `half` around the rounded position
+ * (clipped to the frame) and added to the frame, companion after
+ * companion.  cube: device n_frames x n x n (any n >= 1); all other arrays
+ * on the host (parang, xc, yc, alpha, beta: n_frames; r, pa0, flux:
+ * n_comp).  alpha > 0, beta > 1, 0 <= half <= 4096.  Synchronous.
+ */
+int graphic_inject(graphic_ctx *ctx, float *cube, int64_t n_frames, int32_t n, const double *parang,
+                   const double *xc, const double *yc, int32_t n_comp, const double *r, const double *pa0,
+                   const double *flux, const double *alpha, const double *beta, int32_t half);
+
+/*
+ * Aperture photometry (Sect. 4.2, recovered flux): out[k] = sum of img over
+ * the pixels whose centres lie within `radius` of (x[k], y[k]) ((col -
+ * x)^2 + (row - y)^2 <= radius^2, FP64).  img: device n x n; x, y, out:
+ * host arrays of n_ap.  Synchronous.
+ */
+int graphic_aperture(graphic_ctx *ctx, const float *img, int32_t n, int32_t n_ap, const double *x, const double *y,
+                     double radius, double *out);
+
 /* ---- uneven batches --------------------------------------------------------- */
 
 /* One cube of a batch: device cubes in/out (n_frames x n x n, out may equal
@@ -367,7 +414,8 @@ int graphic_get_precision(graphic_ctx *ctx, int32_t *precision);
 #define GRAPHIC_K_BATCH 7
 #define GRAPHIC_K_REG_ARGMAX 8
 #define GRAPHIC_K_REG_FIT 9
-#define GRAPHIC_K_COUNT 10
+#define GRAPHIC_K_BIN 10
+#define GRAPHIC_K_COUNT 11
 
 /* enable != 0: bracket every kernel launch of the context with CUDA events
  * on its stream and accumulate per-kernel device time and launch counts;

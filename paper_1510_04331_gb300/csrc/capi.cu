@@ -1713,6 +1713,112 @@ int graphic_register(graphic_ctx *c, const float *in, int64_t T, int32_t n, doub
   return end_call(c);
 }
 
+int graphic_bin_median(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, int32_t B) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  int rc = check_cube(in, out, T, n);
+  if (rc) return rc;
+  if (B < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "B must be >= 1");
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  if ((rc = begin_call(c))) return rc;
+  int launched = 0;
+  prof_begin(c, GRAPHIC_K_BIN);
+  cudaError_t e = launch_bin_median(in, out, T, n, B, c->d_status, c->stream, &launched);
+  prof_end(c);
+  if (c->prof && launched > 1) c->prof_extra[GRAPHIC_K_BIN] += launched - 1;
+  if (e != cudaSuccess) return cuda_fail(e, "binning kernel");
+  return end_call(c);
+}
+
+int graphic_bin_mean(const double *v, int64_t n, int32_t B, double *out) {
+  if (n < 0 || B < 1 || (n > 0 && (!v || !out))) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
+  for (int64_t g = 0; g * B < n; g++) {
+    const int64_t f0 = g * B, f1 = std::min<int64_t>(n, f0 + B);
+    double s = 0.0;
+    for (int64_t f = f0; f < f1; f++) s += v[f];
+    out[g] = s / (double)(f1 - f0);
+  }
+  return GRAPHIC_OK;
+}
+
+int graphic_inject(graphic_ctx *c, float *cube, int64_t T, int32_t n, const double *parang, const double *xc,
+                   const double *yc, int32_t n_comp, const double *r, const double *pa0, const double *flux,
+                   const double *alpha, const double *beta, int32_t half) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (T < 0 || n < 1 || n_comp < 0 || half < 0 || half > 4096) return fail(GRAPHIC_ERR_INVALID_ARG, "bad sizes");
+  if (T == 0 || n_comp == 0) return GRAPHIC_OK;
+  if (!cube || !parang || !xc || !yc || !r || !pa0 || !flux || !alpha || !beta)
+    return fail(GRAPHIC_ERR_INVALID_ARG, "null buffer");
+  if (T > INT32_MAX) return fail(GRAPHIC_ERR_INVALID_ARG, "too many frames");
+  const double PI = 3.14159265358979323846;
+  std::vector<double> pos((size_t)T * n_comp * 2);
+  std::vector<int> win((size_t)T * n_comp * 2);
+  std::vector<float> amp((size_t)T * n_comp), shape((size_t)T * 2);
+  for (int j = 0; j < n_comp; j++)
+    if (!std::isfinite(r[j]) || !std::isfinite(pa0[j]) || !std::isfinite(flux[j]))
+      return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite companion parameter");
+  for (int64_t t = 0; t < T; t++) {
+    if (!(alpha[t] > 0) || !(beta[t] > 1) || !std::isfinite(alpha[t]) || !std::isfinite(beta[t]) ||
+        !std::isfinite(parang[t]) || !std::isfinite(xc[t]) || !std::isfinite(yc[t]))
+      return fail(GRAPHIC_ERR_INVALID_ARG, "alpha > 0, beta > 1 and finite angles / centres required");
+    shape[2 * t] = (float)(1.0 / (alpha[t] * alpha[t]));
+    shape[2 * t + 1] = (float)beta[t];
+    for (int j = 0; j < n_comp; j++) {
+      const size_t q = (size_t)t * n_comp + j;
+      const double ang = (pa0[j] + parang[t]) * PI / 180.0;
+      const double xp = xc[t] + r[j] * cos(ang), yp = yc[t] + r[j] * sin(ang);
+      pos[2 * q] = xp;
+      pos[2 * q + 1] = yp;
+      const double fr = floor(yp + 0.5), fc = floor(xp + 0.5);
+      // a window entirely off the frame is skipped by the kernel's bounds test; keep the ints in range
+      win[2 * q] = (int)std::max(-1e9, std::min(1e9, fr));
+      win[2 * q + 1] = (int)std::max(-1e9, std::min(1e9, fc));
+      amp[q] = (float)(flux[j] * (beta[t] - 1.0) / (PI * alpha[t] * alpha[t]));
+    }
+  }
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_pos = pb.add(pos.data(), pos.size() * sizeof(double));
+  const size_t o_win = pb.add(win.data(), win.size() * sizeof(int));
+  const size_t o_amp = pb.add(amp.data(), amp.size() * sizeof(float));
+  const size_t o_shape = pb.add(shape.data(), shape.size() * sizeof(float));
+  int rc;
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  cudaError_t e = launch_inject(cube, T, n, n_comp, at<double>(c, o_pos), at<int>(c, o_win), at<float>(c, o_amp),
+                                at<float>(c, o_shape), half, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "injection kernel");
+  return end_call(c);
+}
+
+int graphic_aperture(graphic_ctx *c, const float *img, int32_t n, int32_t n_ap, const double *x, const double *y,
+                     double radius, double *out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  if (n < 1 || n_ap < 0 || !(radius >= 0) || !std::isfinite(radius)) return fail(GRAPHIC_ERR_INVALID_ARG, "bad sizes");
+  if (n_ap == 0) return GRAPHIC_OK;
+  if (!img || !x || !y || !out) return fail(GRAPHIC_ERR_INVALID_ARG, "null buffer");
+  std::vector<double> xy((size_t)n_ap * 2);
+  for (int k = 0; k < n_ap; k++) {
+    if (!std::isfinite(x[k]) || !std::isfinite(y[k])) return fail(GRAPHIC_ERR_INVALID_ARG, "non-finite position");
+    xy[2 * k] = x[k];
+    xy[2 * k + 1] = y[k];
+  }
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_xy = pb.add(xy.data(), xy.size() * sizeof(double));
+  int rc;
+  if ((rc = ensure((void **)&c->d_prep, &c->prep_bytes, std::max<size_t>(4096, (size_t)n_ap * sizeof(double)),
+                   false)))
+    return rc;
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  double *d_out = reinterpret_cast<double *>(c->d_prep);
+  cudaError_t e = launch_aperture(img, n, n_ap, at<double>(c, o_xy), radius, d_out, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "aperture kernel");
+  CK(cudaMemcpyAsync(out, d_out, (size_t)n_ap * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return end_call(c);
+}
+
 int graphic_profile(graphic_ctx *c, int enable) {
   if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
   c->prof = enable != 0;
@@ -1739,7 +1845,7 @@ int graphic_profile_read(graphic_ctx *c, double *ms, int64_t *launches, int32_t 
 const char *graphic_kernel_name(int32_t k) {
   static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_median", "rot_pass1",
                                               "rot_pass2", "rot_pass3", "collapse_median", "batch_persistent",
-                                              "register_argmax", "register_fit"};
+                                              "register_argmax", "register_fit", "bin_median"};
   return (k >= 0 && k < GRAPHIC_K_COUNT) ? names[k] : nullptr;
 }
 

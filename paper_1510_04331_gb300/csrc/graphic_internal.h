@@ -201,4 +201,16 @@ size_t register_keys_bytes(long long T);
 cudaError_t launch_register_argmax(const RegArgs &a, unsigned long long *keys, cudaStream_t st);
 cudaError_t launch_register_fit(const RegArgs &a, unsigned long long *keys, cudaStream_t st);
 
+// photometry.cu: binning, fake companions, apertures (Sect. 4.2, 4.3)
+// out: ceil(T / B) frames; *launched receives the kernel count
+cudaError_t launch_bin_median(const float *in, float *out, long long T, int n, int B, int *status, cudaStream_t st,
+                              int *launched = nullptr);
+// pos: [T][n_comp] (x, y) FP64; win: [T][n_comp] (row, col) of the window
+// centre; amp: [T][n_comp] Moffat peak; shape: [T] (1 / alpha^2, beta), FP32
+cudaError_t launch_inject(float *cube, long long T, int n, int n_comp, const double *pos, const int *win,
+                          const float *amp, const float *shape, int half, cudaStream_t st);
+// xy: [n_ap] (x, y); out: [n_ap] device FP64
+cudaError_t launch_aperture(const float *img, int n, int n_ap, const double *xy, double radius, double *out,
+                            cudaStream_t st);
+
 }  // namespace graphic

@@ -31,7 +31,7 @@ ERRORS = {
     -7: "GRAPHIC_ERR_INTERNAL",
 }
 KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median",
-           "batch_persistent", "register_argmax", "register_fit"]
+           "batch_persistent", "register_argmax", "register_fit", "bin_median"]
 BATCH_PER_CUBE = 0
 BATCH_PERSISTENT = 1
 BATCH_GROUPED = 2
@@ -120,6 +120,10 @@ _SIGS = {
     "graphic_bad_pixel_map": [_P, _P, _I32, ctypes.c_double, _P],
     "graphic_bad_pixel_fix": [_P, _P, _I64, _I32, _P],
     "graphic_register": [_P, _P, _I64, _I32, ctypes.c_double, _I32, _I32, _I32, _I32, _P, _P],
+    "graphic_bin_median": [_P, _P, _P, _I64, _I32, _I32],
+    "graphic_bin_mean": [_D, _I64, _I32, _D],
+    "graphic_inject": [_P, _P, _I64, _I32, _D, _D, _D, _I32, _D, _D, _D, _D, _D, _I32],
+    "graphic_aperture": [_P, _P, _I32, _I32, _D, _D, ctypes.c_double, _D],
     "graphic_reduce_host": [_P, _P, _I64, _I32, _D, _D, _D, ctypes.c_double, ctypes.c_double, _D, _I32, _P],
     "graphic_profile": [_P, ctypes.c_int],
     "graphic_profile_read": [_P, _D, ctypes.POINTER(_I64), _I32],
@@ -415,6 +419,51 @@ class Context:
                                       None if iters is None else _P(iters.data_ptr())))
         return out
 
+    def graphic_bin_median(self, cube, B, out=None):
+        """Median of every B consecutive frames (the last group may be
+        shorter): a (ceil(T / B), n, n) CUDA tensor."""
+        import torch
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        if out is None:
+            out = torch.empty(((T + int(B) - 1) // max(1, int(B)), n, n), dtype=torch.float32, device=cube.device)
+        self._stream()
+        _check(lib().graphic_bin_median(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, int(B)))
+        return out
+
+    def graphic_inject(self, cube, parang, xc, yc, r, pa0, flux, alpha, beta, half):
+        """In place: Moffat companions (radius r, position angle pa0 + parang,
+        total flux) around the per-frame centres (xc, yc)."""
+        cube = _cube(cube)
+        T, n = cube.shape[0], cube.shape[1]
+        pa, pa_p = _f64(parang, T)
+        x, x_p = _f64(xc, T)
+        y, y_p = _f64(yc, T)
+        al, al_p = _f64(alpha, T)
+        be, be_p = _f64(beta, T)
+        rr = np.ascontiguousarray(np.atleast_1d(np.asarray(r, np.float64)))
+        k = len(rr)
+        p0, p0_p = _f64(pa0, k)
+        fl, fl_p = _f64(flux, k)
+        self._stream()
+        _check(lib().graphic_inject(self.h, _P(cube.data_ptr()), T, n, pa_p, x_p, y_p, k, rr.ctypes.data_as(_D), p0_p,
+                                    fl_p, al_p, be_p, int(half)))
+        return cube
+
+    def graphic_aperture(self, img, x, y, radius):
+        """FP64 sums of the n x n CUDA image over the discs of `radius` around (x, y)."""
+        import torch
+        if not (isinstance(img, torch.Tensor) and img.is_cuda and img.dtype == torch.float32 and img.dim() == 2
+                and img.is_contiguous() and img.shape[0] == img.shape[1]):
+            raise GraphicError(-1, "img must be a contiguous CUDA float32 n x n tensor")
+        xs = np.ascontiguousarray(np.atleast_1d(np.asarray(x, np.float64)))
+        ys, ys_p = _f64(y, len(xs))
+        out = np.zeros(len(xs))
+        self._stream()
+        _check(lib().graphic_aperture(self.h, _P(img.data_ptr()), img.shape[0], len(xs), xs.ctypes.data_as(_D), ys_p,
+                                      float(radius), out.ctypes.data_as(_D)))
+        return out
+
     def set_precision(self, precision: int):
         """PREC_FP32 (default), PREC_BF16X3 or PREC_FP16X3: arithmetic of the
         line passes for frames of n = 1024 (tensor-core DFT stages)."""
@@ -580,3 +629,24 @@ def graphic_reduce_host(cube_host, dx, dy, parang, fwhm, n_fwhm, edges, device=0
 
 def graphic_register(cube, thresh, R, min_size, max_size, w, out=None, iters=None):
     return context().graphic_register(cube, thresh, R, min_size, max_size, w, out, iters)
+
+
+def graphic_bin_median(cube, B, out=None):
+    return context().graphic_bin_median(cube, B, out)
+
+
+def bin_mean(values, B):
+    """Mean of every B consecutive values (the angle or time of a median bin)."""
+    v = np.ascontiguousarray(np.asarray(values, np.float64))
+    out = np.zeros((len(v) + int(B) - 1) // max(1, int(B)))
+    _check(lib().graphic_bin_mean(v.ctypes.data_as(_D), len(v), int(B), out.ctypes.data_as(_D)))
+    return out
+
+
+def graphic_inject(cube, parang, xc, yc, r, pa0, flux, alpha, beta, half):
+    return context().graphic_inject(cube, parang, xc, yc, r, pa0, flux, alpha, beta, half)
+
+
+def graphic_aperture(img, x, y, radius):
+    return context().graphic_aperture(img, x, y, radius)
+

@@ -54,6 +54,19 @@ def test_host_side_checks_without_gpu(lib):
     assert graphic.KERNELS == [lib.graphic_kernel_name(k).decode() for k in range(len(graphic.KERNELS))]
 
 
+def test_bin_mean_host_helper(lib):
+    """Group means of the bin angles / times (host code of the C ABI)."""
+    import numpy as np
+    from paper_1510_04331_gb300 import graphic
+    v = np.random.default_rng(1).uniform(-80, 80, 103)
+    for B in (1, 10, 50, 103, 200):
+        want = np.array([v[g:g + B].mean() for g in range(0, 103, B)])
+        assert np.allclose(graphic.bin_mean(v, B), want, rtol=0, atol=1e-12)
+    assert np.array_equal(graphic.bin_mean(v, 1), v)
+    with pytest.raises(graphic.GraphicError):
+        graphic.bin_mean(v, 0)
+
+
 def test_server_host_side_checks_without_gpu(lib):
     assert lib.graphic_server_create(None, None) == -1
     assert lib.graphic_server_submit(None, None, None) == -1
