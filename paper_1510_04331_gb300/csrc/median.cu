@@ -53,6 +53,11 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Position of the (r+1)-th set bit of x (r = 0 for the lowest), r < popc(x):
 // bisection on the popcounts of the low 16, 8, 4, 2 and 1 bits.
@@ -706,20 +711,32 @@ __device__ __forceinline__ void band_toggle(const uint16_t *code, uint32_t *bm, 
   cb += (cd == CODE_BELOW) ? sign : 0;
 }
 
+// Sweep blocks: the CTA's warps step through their chunks in lockstep, SWK
+// queries at a time, so that the values of a block (one 16-byte copy per
+// frame for the 4 pixels) and its residuals (one 16-byte store per frame)
+// move as whole float4s instead of 4-byte accesses to 32 frames per warp.
+constexpr int SWK = 8;
+constexpr size_t SW_BLOCK_BYTES = (size_t)SWK * 32 * 16;   // [SWK][32 chunks] float4
+
 // Shared-memory carve-up of adi_band_kernel (bytes), for tcap >= T and
-// bitmap width wmax words per lane.
+// bitmap width wmax words per lane.  Late (sweep-time) tenants of dead
+// regions: bitmaps, staged gates and the residual block in the key area,
+// the double-buffered value blocks in the histogram area.
 struct BandSmem {
-  size_t a, code, bk, bidx, hist, brank, perm, total;
+  size_t a, code, bk, bidx, hist, brank, perm, total, obuf;
   __host__ __device__ BandSmem(int tcap, int wmax) {
     const size_t bcm = 32 * (size_t)wmax;
     const size_t keys_b = (size_t)BAND_PPC * tcap * 4;
-    const size_t late_b = (size_t)BAND_PPC * wmax * 32 * 4 + 2 * (size_t)tcap * 4;  // bitmaps + 2 staged gates
+    // bitmaps + 2 staged gates + the residual block
+    const size_t late_b = (size_t)BAND_PPC * wmax * 32 * 4 + 2 * (size_t)tcap * 4 + SW_BLOCK_BYTES;
     a = 0;
+    obuf = (size_t)BAND_PPC * wmax * 32 * 4 + 2 * (size_t)tcap * 4;
     code = keys_b > late_b ? keys_b : late_b;
     bk = code + (size_t)BAND_PPC * tcap * 2;
     bidx = bk + (size_t)BAND_PPC * bcm * 4;
     hist = bidx + (size_t)BAND_PPC * bcm * 2;
     hist = (hist + 15) & ~(size_t)15;
+    static_assert((size_t)BAND_PPC * 512 * 4 >= 2 * SW_BLOCK_BYTES, "value blocks live in the histogram area");
     brank = hist + (size_t)BAND_PPC * 512 * 4;
     perm = brank + (size_t)BAND_PPC * 64 * 8;
     total = perm + (size_t)tcap * 2;
@@ -777,7 +794,6 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
   for (int s = threadIdx.x; s < T; s += 32 * BAND_PPC) perm_s[s] = (uint16_t)__ldg(&a.perm[s]);
   __syncthreads();
   const int ann = ann_s[w];
-  const long long p = p0 + w;
   if (!any) {
     for (int i = threadIdx.x; i < T * BAND_PPC; i += 32 * BAND_PPC)
       a.out[(long long)perm_s[i / BAND_PPC] * NN + p0 + (i % BAND_PPC)] = 0.0f;
@@ -899,18 +915,14 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
     }
   }
   __syncthreads();
-  if (ann < 0) {
-    for (int i = lane; i < T; i += 32) a.out[(long long)perm_s[i] * NN + p] = 0.0f;
-    return;
-  }
-  if (fail) {
-    if (lane == 0) atomicOr(a.status, STATUS_INTERNAL);
-    return;
-  }
+  // pixels outside the annuli and failed warps take part in the lockstep
+  // sweep (their residuals are 0) so that the CTA's barriers stay uniform
+  if (fail && ann >= 0 && lane == 0) atomicOr(a.status, STATUS_INTERNAL);
+  const bool act = ann >= 0 && !fail;
   // gate of this pixel's annulus: staged copy, or global memory for a third
   // annulus inside one 4-pixel group
   const uint32_t *gate = gate_ann[0] == ann ? gate_all : (gate_ann[1] == ann ? gate_all + tcap : nullptr);
-  const int2 *gate_g = reinterpret_cast<const int2 *>(a.lr + (size_t)ann * T * 2);
+  const int2 *gate_g = reinterpret_cast<const int2 *>(a.lr + (size_t)(ann < 0 ? 0 : ann) * T * 2);
   auto gate_at = [&](int i) -> uint32_t {
     if (gate) return gate[i];
     const int2 v = __ldg(&gate_g[i]);
@@ -922,14 +934,28 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
     const int r = s >> 5;
     return (int)brank[64 + r] + __popc(brank[r] & ((1u << (s & 31)) - 1u));
   };
-
-  // ---- 4. chunk-start bitmap and BELOW count of each lane --------------
   const int C = (T + 31) / 32;
   const int c = lane;
   const int i0 = c * C;
   const int i1 = min(T, i0 + C);
+  const int nblk = (C + SWK - 1) / SWK;
+  float4 *vbuf = reinterpret_cast<float4 *>(hist_all);                       // [2][SWK][32]
+  float *obuf = reinterpret_cast<float *>(bsm_raw + L.obuf);                // [SWK][32][4]
+  // values of block b: frame perm[c' C + b SWK + kk], the group's 4 pixels
+  auto prefetch = [&](int b) {
+    float4 *dst = vbuf + (b & 1) * SWK * 32;
+    for (int q = threadIdx.x; q < SWK * 32; q += 32 * BAND_PPC) {
+      const int kk = q >> 5, cc = q & 31;
+      const int i = cc * C + b * SWK + kk;
+      if (b * SWK + kk < C && i < T) cp_async16(dst + q, a.in + (long long)perm_s[i] * NN + p0);
+    }
+    cp_async_commit();
+  };
+  prefetch(0);   // the histograms are dead: overlap the first block with the bitmaps
+
+  // ---- 4. chunk-start bitmap and BELOW count of each lane --------------
   int cb = 0;
-  if (i0 < T) {
+  if (act && i0 < T) {
     const uint32_t g0 = gate_at(i0);
     const int L0 = (int)(g0 & 0xffffu), R0 = (int)(g0 >> 16);
     for (int wd = 0; wd < W; wd++) {
@@ -946,73 +972,93 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
   }
   __syncwarp();
 
-  // ---- 5. per-lane sweep ------------------------------------------------
+  // ---- 5. per-lane sweep, SWK queries per block -------------------------
   // State: word wi of the bitmap column holds the t-th set bit, base = set
   // bits in words < wi.  Gates of band annuli are monotone (host check):
   // frames [L, L') enter the reference set, frames [R, R') leave it.
-  if (i0 < T) {
+  int Lc = 0, Rc = 0, wi = 0, base = 0;
+  bool lane_ok = act && i0 < T;
+  if (lane_ok) {
     const uint32_t g0 = gate_at(i0);
-    int Lc = (int)(g0 & 0xffffu), Rc = (int)(g0 >> 16);
-    int wi = 0, base = 0;
-    const float *src = a.in + p;
-    float v0 = src[(long long)perm_s[i0] * NN];
-    float v1 = (i0 + 1 < i1) ? src[(long long)perm_s[i0 + 1] * NN] : 0.f;
-    float v2 = (i0 + 2 < i1) ? src[(long long)perm_s[i0 + 2] * NN] : 0.f;
-    for (int i = i0; i < i1; i++) {
-      const float v = v0;
-      v0 = v1;
-      v1 = v2;
-      if (i + 3 < i1) v2 = src[(long long)perm_s[i + 3] * NN];
-      const uint32_t gi = gate_at(i);
-      const int Ln = (int)(gi & 0xffffu), Rn = (int)(gi >> 16);
-      // frames [Lc, Ln) enter, [Rc, Rn) leave: the first two of each run
-      // without branches (the usual case is one or two), any others in a loop
-      band_toggle(code, bm, c, Lc, Lc < Ln, 1, wi, base, cb);
-      band_toggle(code, bm, c, Lc + 1, Lc + 1 < Ln, 1, wi, base, cb);
-      for (int s = Lc + 2; s < Ln; s++) band_toggle(code, bm, c, s, true, 1, wi, base, cb);
-      band_toggle(code, bm, c, Rc, Rc < Rn, -1, wi, base, cb);
-      band_toggle(code, bm, c, Rc + 1, Rc + 1 < Rn, -1, wi, base, cb);
-      for (int s = Rc + 2; s < Rn; s++) band_toggle(code, bm, c, s, true, -1, wi, base, cb);
-      Lc = Ln;
-      Rc = Rn;
-      const int nset = Lc + (T - Rc);
-      const int t = ((nset - 1) >> 1) - cb;
-      uint32_t wd = bm[wi * 32 + c];
-      int pc = __popc(wd);
-      while (t < base && wi > 0) {
-        wi--;
-        wd = bm[wi * 32 + c];
-        pc = __popc(wd);
-        base -= pc;
-      }
-      while (t >= base + pc && wi + 1 < W) {
-        base += pc;
-        wi++;
-        wd = bm[wi * 32 + c];
-        pc = __popc(wd);
-      }
-      if (t < base || t >= base + pc) {
-        fail = true;
-        break;
-      }
-      float med = key2f(bk[wi * 32 + nth_set(wd, t - base)]);
-      if ((nset & 1) == 0) {
-        int p2;
-        if (t + 1 < base + pc) {
-          p2 = wi * 32 + nth_set(wd, t - base + 1);
-        } else {
-          p2 = band_next_set(bm, c, (wi + 1) * 32, W);
-          if (p2 < 0) {
-            fail = true;
-            break;
-          }
+    Lc = (int)(g0 & 0xffffu);
+    Rc = (int)(g0 >> 16);
+  }
+  for (int b = 0; b < nblk; b++) {
+    if (b + 1 < nblk) {
+      prefetch(b + 1);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    __syncthreads();   // block b's values are in; block b-1's residuals are written out
+    const float4 *vb = vbuf + (b & 1) * SWK * 32;
+    for (int kk = 0; kk < SWK; kk++) {
+      const int i = i0 + b * SWK + kk;
+      if (b * SWK + kk >= C || i >= i1) break;
+      float res = 0.0f;
+      if (lane_ok) {
+        const uint32_t gi = gate_at(i);
+        const int Ln = (int)(gi & 0xffffu), Rn = (int)(gi >> 16);
+        // frames [Lc, Ln) enter, [Rc, Rn) leave: the first two of each run
+        // without branches (the usual case is one or two), any others in a loop
+        band_toggle(code, bm, c, Lc, Lc < Ln, 1, wi, base, cb);
+        band_toggle(code, bm, c, Lc + 1, Lc + 1 < Ln, 1, wi, base, cb);
+        for (int s = Lc + 2; s < Ln; s++) band_toggle(code, bm, c, s, true, 1, wi, base, cb);
+        band_toggle(code, bm, c, Rc, Rc < Rn, -1, wi, base, cb);
+        band_toggle(code, bm, c, Rc + 1, Rc + 1 < Rn, -1, wi, base, cb);
+        for (int s = Rc + 2; s < Rn; s++) band_toggle(code, bm, c, s, true, -1, wi, base, cb);
+        Lc = Ln;
+        Rc = Rn;
+        const int nset = Lc + (T - Rc);
+        const int t = ((nset - 1) >> 1) - cb;
+        uint32_t wd = bm[wi * 32 + c];
+        int pc = __popc(wd);
+        while (t < base && wi > 0) {
+          wi--;
+          wd = bm[wi * 32 + c];
+          pc = __popc(wd);
+          base -= pc;
         }
-        med = (med + key2f(bk[p2])) * 0.5f;
+        while (t >= base + pc && wi + 1 < W) {
+          base += pc;
+          wi++;
+          wd = bm[wi * 32 + c];
+          pc = __popc(wd);
+        }
+        if (t >= base && t < base + pc) {
+          const int pos = nth_set(wd, t - base);
+          float med = key2f(bk[wi * 32 + pos]);
+          if ((nset & 1) == 0) {
+            // the next member: a higher bit of this word, else the next word's first
+            const uint32_t rest = pos < 31 ? (wd & (0xfffffffeu << pos)) : 0u;
+            const int p2 = rest ? wi * 32 + __ffs(rest) - 1 : band_next_set(bm, c, (wi + 1) * 32, W);
+            if (p2 >= 0)
+              med = (med + key2f(bk[p2])) * 0.5f;
+            else
+              lane_ok = false;
+          }
+          if (lane_ok) {
+            const float4 v4 = vb[kk * 32 + c];
+            const float v = w == 0 ? v4.x : (w == 1 ? v4.y : (w == 2 ? v4.z : v4.w));
+            res = v - med;
+          }
+        } else {
+          lane_ok = false;
+        }
+        if (!lane_ok) atomicOr(a.status, STATUS_INTERNAL);
       }
-      a.out[(long long)perm_s[i] * NN + p] = v - med;
+      obuf[(kk * 32 + c) * 4 + w] = res;
+    }
+    __syncthreads();   // block b's residuals are complete
+    for (int q = threadIdx.x; q < SWK * 32; q += 32 * BAND_PPC) {
+      const int kk = q >> 5, cc = q & 31;
+      const int i = cc * C + b * SWK + kk;
+      if (b * SWK + kk < C && i < T) {
+        const float4 r4 = reinterpret_cast<const float4 *>(obuf)[q];
+        *reinterpret_cast<float4 *>(a.out + (long long)perm_s[i] * NN + p0) = r4;
+      }
     }
   }
-  if (fail) atomicOr(a.status, STATUS_INTERNAL);
 }
 
 int pow2_at_least(long long x, int lo) {
