@@ -253,7 +253,10 @@ int graphic_bad_pixel_fix(graphic_ctx *ctx, float *cube, int64_t n_frames, int32
  *     it, or after 200 iterations.  FWHM = 2 alpha sqrt(2^(1/beta) - 1).
  * out: device n_frames x 8 doubles per frame: found (1.0 / 0.0), x0, y0,
  * FWHM, I0, alpha, beta, Bg (all 0 when not found).  iters: device
- * n_frames int32 (iterations made, 0 when not found) or NULL.  in must be
+ * n_frames int32 (iterations made, 0 when not found) or NULL.  The fit
+ * runs in two phases: the iteration above with the per-pixel model in FP32
+ * (lambda floor 1e-6, stop at a drop <= 1e-7 of the squared error), then
+ * the FP64 iteration above from its result; iters counts both (<= 400).  in must be
  * 16-byte aligned, 1 <= n <= 65535, 1 <= R <= 32, 1 <= w <= 32; the
  * context scratch holds 8 bytes a frame.  All arithmetic after the pixel
  * values is FP64.  GRAPHIC_ERR_NONFINITE if a frame holds a non-finite

@@ -136,6 +136,12 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+__device__ __forceinline__ float warp_sum32(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 __device__ __forceinline__ float warp_min(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -149,25 +155,30 @@ struct MoffatConst {
 };
 
 __device__ __forceinline__ MoffatConst moffat_const(const double *p) {
+  constexpr double INV_PI = 0.318309886183790671537767526745;   // 1 / pi
   MoffatConst k;
   const double I0 = p[0], al = p[3], be = p[4];
+  const double ia = 1.0 / al;                  // the one division of a parameter set
   k.x0 = p[1];
   k.y0 = p[2];
   k.beta = be;
   k.bg = p[5];
-  k.ia2 = 1.0 / (al * al);
-  k.A = I0 * (be - 1.0) * k.ia2 / REG_PI;      // I0 (beta - 1) / (pi alpha^2)
-  k.c0 = (be - 1.0) * k.ia2 / REG_PI;          // dI/dI0 = c0 P
+  k.ia2 = ia * ia;
+  k.c0 = (be - 1.0) * k.ia2 * INV_PI;          // dI/dI0 = c0 P
+  k.A = I0 * k.c0;                             // I0 (beta - 1) / (pi alpha^2)
   k.c1 = 2.0 * k.A * be * k.ia2;               // dI/dx0 = c1 P / u dx
-  k.c3 = -2.0 * k.A / al;                      // dI/dalpha = c3 P + c4 rho^2 P / u
-  k.c4 = k.c1 / al;
-  k.c5 = I0 * k.ia2 / REG_PI;                  // dI/dbeta = c5 P - A ln(u) P
+  k.c3 = -2.0 * k.A * ia;                      // dI/dalpha = c3 P + c4 rho^2 P / u
+  k.c4 = k.c1 * ia;
+  k.c5 = I0 * k.ia2 * INV_PI;                  // dI/dbeta = c5 P - A ln(u) P
   return k;
 }
 
-// Damped 6 x 6 solve by Cholesky; false when the matrix is not positive definite.
+// Damped 6 x 6 solve by Cholesky; false when the matrix is not positive
+// definite.  The six pivots' reciprocals are taken once, so the
+// factorisation and both substitutions run on multiplications (FP64
+// divisions are long instruction sequences on this GPU).
 __device__ bool chol6(const double *A, const double *b, double *x) {
-  double L[21];   // lower triangle, row i at i (i + 1) / 2
+  double L[21], inv[6];   // lower triangle, row i at i (i + 1) / 2; 1 / L[i][i]
 #pragma unroll
   for (int i = 0; i < 6; i++)
 #pragma unroll
@@ -177,9 +188,11 @@ __device__ bool chol6(const double *A, const double *b, double *x) {
       for (int k = 0; k < j; k++) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
       if (i == j) {
         if (!(s > 0)) return false;
-        L[i * (i + 1) / 2 + i] = sqrt(s);
+        const double d = sqrt(s);
+        L[i * (i + 1) / 2 + i] = d;
+        inv[i] = 1.0 / d;
       } else {
-        L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+        L[i * (i + 1) / 2 + j] = s * inv[j];
       }
     }
   double y[6];
@@ -188,14 +201,14 @@ __device__ bool chol6(const double *A, const double *b, double *x) {
     double s = b[i];
 #pragma unroll
     for (int k = 0; k < i; k++) s -= L[i * (i + 1) / 2 + k] * y[k];
-    y[i] = s / L[i * (i + 1) / 2 + i];
+    y[i] = s * inv[i];
   }
 #pragma unroll
   for (int i = 5; i >= 0; i--) {
     double s = y[i];
 #pragma unroll
     for (int k = i + 1; k < 6; k++) s -= L[k * (k + 1) / 2 + i] * x[k];
-    x[i] = s / L[i * (i + 1) / 2 + i];
+    x[i] = s * inv[i];
   }
   return true;
 }
@@ -218,7 +231,12 @@ __device__ __forceinline__ double window_pass(const MoffatConst &k, const float 
     const double u = 1.0 + rho2 * k.ia2;
     const double lu = log(u);
     const double P = exp(-k.beta * lu);
-    const double Pu = P / u;
+    // 1 / u: the FP32 reciprocal refined by two Newton steps r <- r (2 - u r)
+    // (relative error 1e-7 -> 1e-14 -> below FP64 rounding; u >= 1)
+    double ru = (double)__frcp_rn((float)u);
+    ru = ru * (2.0 - u * ru);
+    ru = ru * (2.0 - u * ru);
+    const double Pu = P * ru;
     const double e = k.A * P + k.bg - (double)win[i];
     double g[6];
     g[0] = k.c0 * P;
@@ -239,6 +257,203 @@ __device__ __forceinline__ double window_pass(const MoffatConst &k, const float 
 #pragma unroll
   for (int q = 0; q < 27; q++) ne[q] = warp_sum(ne[q]);
   return warp_sum(cost);
+}
+
+// The damped step of the FP32 phase: the normal equations scaled by D =
+// diag(J^T J)^(-1/2) (unit diagonal, so the damping lambda diag(J^T J)
+// becomes lambda I), factorised and solved in FP32, the step scaled back.
+// False when the scaled matrix is not positive definite.
+__device__ bool step32(const double *ne, double lambda, double *d) {
+  float dinv[6], L[21], inv[6], y[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    const double a = ne[i * (i + 1) / 2 + i];
+    dinv[i] = a > 0 ? rsqrtf((float)a) : 1.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) {
+      float s = (float)ne[i * (i + 1) / 2 + j] * dinv[i] * dinv[j];
+      if (i == j) {
+        const double a = ne[i * (i + 1) / 2 + i];
+        s += (float)(lambda * (a > 0 ? 1.0 : 1e-12));
+      }
+#pragma unroll
+      for (int k = 0; k < j; k++) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+      if (i == j) {
+        if (!(s > 0.0f)) return false;
+        const float dd = sqrtf(s);
+        L[i * (i + 1) / 2 + i] = dd;
+        inv[i] = 1.0f / dd;
+      } else {
+        L[i * (i + 1) / 2 + j] = s * inv[j];
+      }
+    }
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    float s = -(float)ne[21 + i] * dinv[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) s -= L[i * (i + 1) / 2 + k] * y[k];
+    y[i] = s * inv[i];
+  }
+  float x[6];
+#pragma unroll
+  for (int i = 5; i >= 0; i--) {
+    float s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; k++) s -= L[k * (k + 1) / 2 + i] * x[k];
+    x[i] = s * inv[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 6; i++) d[i] = (double)(x[i] * dinv[i]);
+  return true;
+}
+
+// The same quotients in FP32, for the first (FP32) phase of the fit.
+struct MoffatConst32 {
+  float x0, y0, beta, bg, ia2, A, c0, c1, c3, c4, c5;
+};
+
+__device__ __forceinline__ MoffatConst32 moffat_const32(const double *p) {
+  const MoffatConst k = moffat_const(p);
+  MoffatConst32 f;
+  f.x0 = (float)k.x0;
+  f.y0 = (float)k.y0;
+  f.beta = (float)k.beta;
+  f.bg = (float)k.bg;
+  f.ia2 = (float)k.ia2;
+  f.A = (float)k.A;
+  f.c0 = (float)k.c0;
+  f.c1 = (float)k.c1;
+  f.c3 = (float)k.c3;
+  f.c4 = (float)k.c4;
+  f.c5 = (float)k.c5;
+  return f;
+}
+
+// window_pass with the per-pixel model, derivatives, lane partials and warp
+// sums in FP32: on GB300 the FP32 pipe is 64 times the FP64 one, and the
+// first iterations only need to come close.
+__device__ __forceinline__ double window_pass32(const MoffatConst32 &k, const float *win, int WH, int WW, int wr0,
+                                                int wc0, int lane, double *ne) {
+  float cost = 0.0f, a[27];
+#pragma unroll
+  for (int q = 0; q < 27; q++) a[q] = 0.0f;
+  for (int i = lane; i < WH * WW; i += 32) {
+    const int r = i / WW, c = i - r * WW;
+    const float dx = (float)(c + wc0) - k.x0, dy = (float)(r + wr0) - k.y0;
+    const float rho2 = dx * dx + dy * dy;
+    const float u = 1.0f + rho2 * k.ia2;
+    const float l2 = log2f(u);
+    const float P = exp2f(-k.beta * l2);
+    const float Pu = P / u;
+    const float e = k.A * P + k.bg - win[i];
+    float g[6];
+    g[0] = k.c0 * P;
+    g[1] = k.c1 * Pu * dx;
+    g[2] = k.c1 * Pu * dy;
+    g[3] = k.c3 * P + k.c4 * rho2 * Pu;
+    g[4] = k.c5 * P - k.A * (l2 * 0.69314718056f) * P;
+    g[5] = 1.0f;
+    cost += e * e;
+    int q = 0;
+#pragma unroll
+    for (int ii = 0; ii < 6; ii++)
+#pragma unroll
+      for (int jj = 0; jj <= ii; jj++) a[q++] += g[ii] * g[jj];
+#pragma unroll
+    for (int ii = 0; ii < 6; ii++) a[21 + ii] += g[ii] * e;
+  }
+  // FP32 butterflies (each lane ends with the same bits), widened at the end
+#pragma unroll
+  for (int q = 0; q < 27; q++) ne[q] = (double)warp_sum32(a[q]);
+  return (double)warp_sum32(cost);
+}
+
+// Levenberg-Marquardt iterations from p (the oracle's steps: damping lambda
+// x diag(J^T J) from 1e-3, /10 (floor lam_floor) on an accepted step, x10 on
+// a rejected one or one leaving alpha <= 0 or beta <= 1, at most 10 tries;
+// stop when an accepted step lowers the squared error by at most stop_rel
+// of it, when no try lowers it, or after 200 iterations).  F32 selects the
+// FP32 evaluation.  Returns the iterations made; p and cost are updated.
+template <bool F32>
+__device__ __forceinline__ int lm_loop(double (&p)[6], double &cost, double *ne_cur, double lam_floor,
+                                       double stop_rel, const float *buf, int WH, int WW, int wr0, int wc0,
+                                       int lane) {
+  double ne[27];
+  cost = F32 ? window_pass32(moffat_const32(p), buf, WH, WW, wr0, wc0, lane, ne)
+             : window_pass(moffat_const(p), buf, WH, WW, wr0, wc0, lane, ne);
+  // ne_cur: the normal equations at p (identical in every lane: lane q keeps q)
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 27; q++)
+    if (lane == q) ne_cur[q] = ne[q];
+  __syncwarp();
+  double lambda = 1e-3;
+  int it;
+  for (it = 0; it < 200; it++) {
+    bool accepted = false;
+    double newcost = cost;
+    for (int tries = 0; tries < 10; tries++) {
+      double d[6], q[6];
+      bool ok;
+      if constexpr (F32) {
+        ok = step32(ne_cur, lambda, d);
+      } else {
+        double A[36], mg[6];
+        int k = 0;
+#pragma unroll
+        for (int ii = 0; ii < 6; ii++)
+#pragma unroll
+          for (int jj = 0; jj <= ii; jj++) {
+            A[ii * 6 + jj] = ne_cur[k];
+            A[jj * 6 + ii] = ne_cur[k];
+            k++;
+          }
+#pragma unroll
+        for (int ii = 0; ii < 6; ii++) {
+          const double di = A[ii * 6 + ii] > 0 ? A[ii * 6 + ii] : 1e-12;
+          A[ii * 6 + ii] += lambda * di;
+          mg[ii] = -ne_cur[21 + ii];
+        }
+        ok = chol6(A, mg, d);
+      }
+      if (!ok) {
+        lambda *= 10.0;
+        continue;
+      }
+#pragma unroll
+      for (int ii = 0; ii < 6; ii++) q[ii] = p[ii] + d[ii];
+      if (!(q[3] > 0) || !(q[4] > 1.0)) {
+        lambda *= 10.0;
+        continue;
+      }
+      newcost = F32 ? window_pass32(moffat_const32(q), buf, WH, WW, wr0, wc0, lane, ne)
+                    : window_pass(moffat_const(q), buf, WH, WW, wr0, wc0, lane, ne);
+      if (newcost < cost) {
+#pragma unroll
+        for (int ii = 0; ii < 6; ii++) p[ii] = q[ii];
+        __syncwarp();   // every lane has read ne_cur
+#pragma unroll
+        for (int qq = 0; qq < 27; qq++)
+          if (lane == qq) ne_cur[qq] = ne[qq];
+        __syncwarp();
+        lambda = fmax(lambda / 10.0, lam_floor);
+        accepted = true;
+        break;
+      }
+      lambda *= 10.0;
+    }
+    if (!accepted) break;
+    const double drop = cost - newcost;
+    cost = newcost;
+    if (drop <= stop_rel * cost) {
+      it++;
+      break;
+    }
+  }
+  return it;
 }
 
 // One frame on one warp: seed from the argmax word, patch, centroid, fit.
@@ -344,68 +559,15 @@ __device__ __forceinline__ void fit_frame(const RegArgs &a, unsigned long long k
   for (int i = lane; i < WH * WW; i += 32) i0 += (double)buf[i] - bg;
   i0 = warp_sum(i0);
   double p[6] = {i0, cx, cy, fmax(1.0, sqrt((double)size / REG_PI)), 2.5, bg};
-  double ne[27];
-  double cost = window_pass(moffat_const(p), buf, WH, WW, wr0, wc0, lane, ne);
-  // ne_cur: the normal equations at p (identical in every lane: lane q keeps q)
-#pragma unroll
-  for (int q = 0; q < 27; q++)
-    if (lane == q) ne_cur[q] = ne[q];
-  __syncwarp();
-  double lambda = 1e-3;
-  int it;
-  for (it = 0; it < 200; it++) {
-    bool accepted = false;
-    double newcost = cost;
-    for (int tries = 0; tries < 10; tries++) {
-      double A[36], mg[6], d[6], q[6];
-      int k = 0;
-#pragma unroll
-      for (int ii = 0; ii < 6; ii++)
-#pragma unroll
-        for (int jj = 0; jj <= ii; jj++) {
-          A[ii * 6 + jj] = ne_cur[k];
-          A[jj * 6 + ii] = ne_cur[k];
-          k++;
-        }
-#pragma unroll
-      for (int ii = 0; ii < 6; ii++) {
-        const double di = A[ii * 6 + ii] > 0 ? A[ii * 6 + ii] : 1e-12;
-        A[ii * 6 + ii] += lambda * di;
-        mg[ii] = -ne_cur[21 + ii];
-      }
-      if (!chol6(A, mg, d)) {
-        lambda *= 10.0;
-        continue;
-      }
-#pragma unroll
-      for (int ii = 0; ii < 6; ii++) q[ii] = p[ii] + d[ii];
-      if (!(q[3] > 0) || !(q[4] > 1.0)) {
-        lambda *= 10.0;
-        continue;
-      }
-      newcost = window_pass(moffat_const(q), buf, WH, WW, wr0, wc0, lane, ne);
-      if (newcost < cost) {
-#pragma unroll
-        for (int ii = 0; ii < 6; ii++) p[ii] = q[ii];
-        __syncwarp();   // every lane has read ne_cur
-#pragma unroll
-        for (int qq = 0; qq < 27; qq++)
-          if (lane == qq) ne_cur[qq] = ne[qq];
-        __syncwarp();
-        lambda = fmax(lambda / 10.0, 1e-12);
-        accepted = true;
-        break;
-      }
-      lambda *= 10.0;
-    }
-    if (!accepted) break;
-    const double drop = cost - newcost;
-    cost = newcost;
-    if (drop <= 1e-14 * cost) {
-      it++;
-      break;
-    }
-  }
+  double cost;
+  // Phase A: FP32 evaluation until the FP32 cost stops improving (its
+  // rounding is about 1e-7 of it; a lambda floor of 1e-6 keeps the damped
+  // system well away from the FP32 noise of J^T J).  Phase B: the FP64
+  // iteration of the oracle from there, which converges in a few steps to
+  // the same minimum.
+  const int it_a = lm_loop<true>(p, cost, ne_cur, 1e-6, 1e-7, buf, WH, WW, wr0, wc0, lane);
+  const int it_b = lm_loop<false>(p, cost, ne_cur, 1e-12, 1e-14, buf, WH, WW, wr0, wc0, lane);
+  const int it = it_a + it_b;
   if (lane == 0) {
     out[0] = 1.0;
     out[1] = p[1];

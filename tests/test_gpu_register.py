@@ -3,11 +3,12 @@ FP64 oracle on identical inputs: the found flags bit for bit (the seed is
 an argmax, the patch a flood fill, both exact), the fitted parameters
 within bounds set by the conditioning of the fit.
 
-Both sides run the same Levenberg-Marquardt steps in FP64; they differ only
-in the summation order of the sums and in the last bit of log / exp, so the
-trajectories agree to rounding.  Perturbing the oracle's start by 1e-12 px
-moves x0, y0 by ~1e-12 px and alpha, beta, I0 by up to 1e-8 relative (the
-stopping test may fire one iteration apart; alpha and beta are strongly
+Both sides end with the same FP64 Levenberg-Marquardt iteration and its
+stopping test (the GPU starts it from an FP32 phase that brings it close),
+so both stop within the stopping tolerance of the same minimum: a drop of
+1e-14 of the squared error leaves ~1e-8 px in x0, y0 (curvature ~4e8 per
+px^2 against a cost ~4e6); perturbing the oracle's start by 1e-12 px moves
+alpha, beta, I0 by up to 1e-8 relative (alpha and beta are strongly
 correlated), hence: x0, y0 within 1e-6 px; FWHM, I0, alpha, beta, Bg
 within 1e-5 relative (Bg: of the peak)."""
 import math
@@ -79,7 +80,7 @@ def test_register_against_oracle(g, n, R, w):
     # steps lower the cost at the rounding level, so which one passes the
     # 1e-14 stopping test depends on rounding (observed: up to 3 apart)
     its = it.cpu().numpy()
-    assert np.array_equal(its > 0, want[:, 0] == 1.0) and its.max() <= 200 and (want_it > 0).sum() == (its > 0).sum()
+    assert np.array_equal(its > 0, want[:, 0] == 1.0) and its.max() <= 400 and (want_it > 0).sum() == (its > 0).sum()
 
 
 def test_register_accuracy_and_frame_selection(g):
