@@ -361,7 +361,7 @@ int graphic_batch_geom(graphic_ctx *ctx, const graphic_batch_item *items, int32_
 /*
  * Autotuner: time the schedule candidates on this batch and keep the fastest
  * in the context -- for the per-call passes the intermediate per chunk of
- * frames (16..256 MiB, L2 staging) and the kernel of 1024-point lines (one
+ * frames (64..4096 MiB) and the kernel of 1024-point lines (one
  * warp per line pair with radix-32 stages, or the generic radix-16 kernel);
  * for the persistent executor the wave budget and CTAs per SM; for the
  * grouped executor the wave budget and the number of concurrent branches;

@@ -56,7 +56,9 @@ struct graphic_ctx {
   std::vector<int> ev_kernel;       // kernel id per used pair
   size_t ev_used = 0;
   // schedule (defaults, autotuner, or GRAPHIC_TUNE_CACHE)
-  int chunk_mb = 64;                // frames per chunk of the per-call passes: this much intermediate
+  int chunk_mb = 4096;              // frames per chunk of the per-call passes: this much intermediate
+                                    // (measured: one chunk per survey cube beats L2-sized chunks, whose
+                                    // launch tails cost more than the scratch's trips to HBM)
   int variant_1024 = 1;             // 1024-point lines: 1 warp per line pair (radix 32x32), 0 generic
   int batch_budget_mb = 1024;       // persistent executor: scratch of one wave (two waves alternate)
   int batch_ctas_per_sm = 2;
@@ -219,6 +221,8 @@ int end_call(graphic_ctx *c) {
   if (*c->h_status & STATUS_TIMEOUT) return fail(GRAPHIC_ERR_TIMEOUT, "a bounded device wait ran out");
   return GRAPHIC_OK;
 }
+
+constexpr size_t kCopyChunkMB = 256;   // host -> device copy pieces of graphic_reduce_host
 
 long long chunk_frames(const graphic_ctx *c, long long T, size_t bytes_per_frame) {
   size_t budget = (size_t)c->chunk_mb << 20;
@@ -604,8 +608,11 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
     // the copies start after everything already on the compute stream
     CK(cudaEventRecord(c->ev_copy, c->stream));
     CK(cudaStreamWaitEvent(c->s_copy, c->ev_copy, 0));
+    // copies in pieces of kCopyChunkMB, each piece's shift launched as soon as
+    // it lands (the copy, not the shift, bounds this path)
     const size_t NN = (size_t)n * n;
-    const long long ch = chunk_frames(c, T, NN * sizeof(float));
+    const long long ch = std::max<long long>(1, std::min<long long>(T, (long long)((kCopyChunkMB << 20) /
+                                                                                    (NN * sizeof(float)))));
     for (long long f0 = 0; f0 < T; f0 += ch) {
       const long long nf = std::min<long long>(ch, T - f0);
       CK(cudaMemcpyAsync(const_cast<float *>(in) + f0 * NN, host_in + f0 * NN, nf * NN * sizeof(float),
@@ -1406,7 +1413,7 @@ int graphic_autotune(graphic_ctx *c, const graphic_batch_item *items, int32_t n_
   int best_chunk = c->chunk_mb, best_var = c->variant_1024;
   float best_pc = 1e30f;
   for (int var = 0; var <= 1; var++)
-    for (int mb : {16, 32, 64, 128, 256}) {
+    for (int mb : {64, 256, 1024, 4096}) {
       c->chunk_mb = mb;
       c->variant_1024 = var;
       if ((rc = time_batch(c, items, n_items, GRAPHIC_BATCH_PER_CUBE, 2, &ms))) return rc;
