@@ -24,6 +24,7 @@
 // Collapse.  Per pixel, radix select (4 passes of 8-bit histograms with
 // warp-aggregated counts) of the lower median, plus the next key for even T.
 #include <cuda_runtime.h>
+#include <type_traits>
 #include <stdint.h>
 
 #include "graphic_internal.h"
@@ -843,38 +844,59 @@ __global__ void __launch_bounds__(32 * BAND_PPC, 3) adi_band_kernel(const AdiArg
     band_select2(kw, T, (uint32_t)blo, (uint32_t)bhi, orv ^ andv, andv, hist, hist + 256, lane, Klo, clt_lo,
                  Khi, clt_hi);
     // ---- 2. ordered extraction -------------------------------------------
+    // First without tie handling: the band is taken as the keys in
+    // [Klo, Khi].  When that set has exactly bhi - blo + 1 members it is the
+    // band (no key equal to a bound had to go outside); otherwise keys equal
+    // to a bound are split by frame order in a second, exact pass.  Both
+    // passes write every frame's code or band entry.
     const int need_lo = blo - (int)clt_lo;
     const int lim_hi = bhi + 1 - (int)clt_hi;
     const unsigned lt = (1u << lane) - 1u;
-    int tlo = 0, thi = 0;
-    for (int base = 0; base < T; base += 32) {
-      const int s = base + lane;
-      const bool valid = s < T;
-      const uint32_t key = valid ? kw[s * BAND_PPC] : 0u;
-      const bool eqlo = valid && key == Klo, eqhi = valid && key == Khi;
-      const unsigned mlo = __ballot_sync(FULL, eqlo), mhi = __ballot_sync(FULL, eqhi);
-      const int ilo = tlo + __popc(mlo & lt), ihi = thi + __popc(mhi & lt);
-      const bool below = valid && (key < Klo || (eqlo && ilo < need_lo));
-      const bool above = valid && !below && (key > Khi || (eqhi && ihi >= lim_hi));
-      const bool inb = valid && !below && !above;
-      const unsigned mb = __ballot_sync(FULL, inb), mbl = __ballot_sync(FULL, below);
-      if (inb) {
-        const int j = nb + __popc(mb & lt);
-        if (j < BCM) {
-          bk[j] = key;
-          bidx[j] = (uint16_t)s;
+    auto extract = [&](auto ties) {
+      constexpr bool TIES = decltype(ties)::value;
+      nb = 0;
+      nbelow = 0;
+      int tlo = 0, thi = 0;
+      for (int base = 0; base < T; base += 32) {
+        const int s = base + lane;
+        const bool valid = s < T;
+        const uint32_t key = valid ? kw[s * BAND_PPC] : 0u;
+        bool below, above;
+        if constexpr (TIES) {
+          const bool eqlo = valid && key == Klo, eqhi = valid && key == Khi;
+          const unsigned mlo = __ballot_sync(FULL, eqlo), mhi = __ballot_sync(FULL, eqhi);
+          const int ilo = tlo + __popc(mlo & lt), ihi = thi + __popc(mhi & lt);
+          below = valid && (key < Klo || (eqlo && ilo < need_lo));
+          above = valid && !below && (key > Khi || (eqhi && ihi >= lim_hi));
+          tlo += __popc(mlo);
+          thi += __popc(mhi);
+        } else {
+          below = valid && key < Klo;
+          above = valid && key > Khi;
         }
-      } else if (valid) {
-        code[s] = below ? CODE_BELOW : CODE_ABOVE;
+        const bool inb = valid && !below && !above;
+        const unsigned mb = __ballot_sync(FULL, inb), mbl = __ballot_sync(FULL, below);
+        if (inb) {
+          const int j = nb + __popc(mb & lt);
+          if (j < BCM) {
+            bk[j] = key;
+            bidx[j] = (uint16_t)s;
+          }
+        } else if (valid) {
+          code[s] = below ? CODE_BELOW : CODE_ABOVE;
+        }
+        if (lane == 0) {
+          brank[base >> 5] = mbl;
+          brank[64 + (base >> 5)] = (uint32_t)nbelow;
+        }
+        nb += __popc(mb);
+        nbelow += __popc(mbl);
       }
-      if (lane == 0) {
-        brank[base >> 5] = mbl;
-        brank[64 + (base >> 5)] = (uint32_t)nbelow;
-      }
-      tlo += __popc(mlo);
-      thi += __popc(mhi);
-      nb += __popc(mb);
-      nbelow += __popc(mbl);
+    };
+    extract(std::false_type{});
+    if (nb != bhi - blo + 1) {
+      __syncwarp();
+      extract(std::true_type{});
     }
     if (nb != bhi - blo + 1 || nb > 32 * W) fail = true;
     __syncwarp();
