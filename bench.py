@@ -89,9 +89,9 @@ def job_throughput(units_per_rank_step, steps, world, max_ms):
 # (bytes per step at that size, source).  Per launch = bytes / launches.
 MEASURED_TRAFFIC = {
     ("adi_median", 2000, 512): (
-        3.620e9,
+        3.619e9,
         "ncu dram bytes of the median PSF launches (general + band) at 200 frames of the survey recipe "
-        "(362.0 MB), scaled x10 to 2000 frames (traffic grows with the frames)"),
+        "(361.9 MB), scaled x10 to 2000 frames (traffic grows with the frames)"),
 }
 
 
