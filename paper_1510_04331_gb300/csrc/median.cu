@@ -238,6 +238,14 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
   }
   const uint32_t k = (uint32_t)((m - 1) / 2);
   uint32_t prefix = 0, pmask = 0, krem = k, cnt = (uint32_t)T;
+  // Candidate list: the pass in which at most `cap` keys still match the
+  // prefix also copies them (in frame order) into the row padding words
+  // (word COL_KS - 1 of rows [w cap, (w + 1) cap), which no key uses), and
+  // the later passes read only the list.
+  const int cap = SMEM ? (int)(T / COL_PPC < 128 ? T / COL_PPC : 128) : 0;
+  uint32_t *cbuf = keys_all + (long long)w * cap * COL_KS + (COL_KS - 1);   // element j at cbuf[j * COL_KS]
+  int nc = -1;                                                            // list length, -1: none yet
+  const unsigned lt = (1u << lane) - 1u;
   for (int pass = 0; pass < 4; pass++) {
     const int shift = 24 - 8 * pass;
     if (((varying >> shift) & 255u) == 0) {   // every key has this digit
@@ -248,10 +256,31 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
 #pragma unroll
     for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0;
     __syncwarp();
+    if (nc >= 0) {
+      for (int j = lane; j < nc; j += 32) {
+        const uint32_t key = cbuf[j * COL_KS];
+        if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
+    } else if (cnt <= (uint32_t)cap) {
+      int len = 0;
+      for (long long t0 = 0; t0 < T; t0 += 32) {
+        const long long t = t0 + lane;
+        const uint32_t key = t < T ? key_at(t) : 0u;
+        const bool match = t < T && (key & pmask) == prefix;
+        const unsigned mm = __ballot_sync(FULL, match);
+        if (match) {
+          cbuf[(len + __popc(mm & lt)) * COL_KS] = key;
+          atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        len += __popc(mm);
+      }
+      nc = len;
+    } else {
 #pragma unroll 4
-    for (long long t = lane; t < T; t += 32) {
-      const uint32_t key = key_at(t);
-      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      for (long long t = lane; t < T; t += 32) {
+        const uint32_t key = key_at(t);
+        if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
     }
     __syncwarp();
     uint32_t d, below;
@@ -266,14 +295,27 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
   if ((m & 1) == 0) {
     uint32_t hi = prefix;
     if (krem + 1 >= cnt) {
-      // smallest key greater than the lower median
+      // smallest key greater than the lower median: from the candidate list
+      // when it holds one (the list's bucket is a contiguous key range, so a
+      // larger key inside it beats every key above it), else from all keys
       uint32_t mn = 0xffffffffu;
-      for (long long t = lane; t < T; t += 32) {
-        const uint32_t key = key_at(t);
-        if (key > prefix && key < mn) mn = key;
-      }
+      if (nc >= 0) {
+        for (int j = lane; j < nc; j += 32) {
+          const uint32_t key = cbuf[j * COL_KS];
+          if (key > prefix && key < mn) mn = key;
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+      }
+      if (nc < 0 || mn == 0xffffffffu) {
+        mn = 0xffffffffu;
+        for (long long t = lane; t < T; t += 32) {
+          const uint32_t key = key_at(t);
+          if (key > prefix && key < mn) mn = key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL, mn, o));
+      }
       hi = mn;
     }
     med = (lo + key2f(hi)) * 0.5f;
