@@ -141,6 +141,7 @@ cudaError_t bin_launch(const float *in, float *out, long long T, long long nn, i
                        cudaStream_t st) {
   const long long G = (T + B - 1) / B;
   const long long bpg = (nn + BIN_THREADS - 1) / BIN_THREADS;
+  if (G * bpg > 0x7fffffffLL) return cudaErrorInvalidConfiguration;   // one block per (bin, 128 pixels)
   bin_median_kernel<W><<<(unsigned)(G * bpg), BIN_THREADS, 0, st>>>(in, out, T, nn, B, bpg, status);
   return cudaGetLastError();
 }
