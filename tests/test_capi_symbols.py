@@ -54,6 +54,23 @@ def test_host_side_checks_without_gpu(lib):
     assert graphic.KERNELS == [lib.graphic_kernel_name(k).decode() for k in range(len(graphic.KERNELS))]
 
 
+def test_new_calls_reject_a_null_context_without_gpu(lib):
+    """Every call added for the later rows checks its arguments on the host
+    before any CUDA call (these run without a GPU)."""
+    calls = [
+        lambda: lib.graphic_register(None, None, 1, 64, 1.0, 8, 3, 400, 6, None, None),
+        lambda: lib.graphic_bin_median(None, None, None, 10, 64, 5),
+        lambda: lib.graphic_inject(None, None, 1, 64, None, None, None, 1, None, None, None, None, None, 5),
+        lambda: lib.graphic_aperture(None, None, 64, 1, None, None, 3.0, None),
+        lambda: lib.graphic_sky_median(None, None, 1, 64, None, None, 0.0, None),
+        lambda: lib.graphic_bad_pixel_map(None, None, 64, 5.0, None),
+        lambda: lib.graphic_bad_pixel_fix(None, None, 1, 64, None),
+    ]
+    for call in calls:
+        assert call() == -1
+        assert b"ctx" in lib.graphic_last_error()
+
+
 def test_bin_mean_host_helper(lib):
     """Group means of the bin angles / times (host code of the C ABI)."""
     import numpy as np
