@@ -11,6 +11,14 @@ of 2000 frames of 512 x 512 (padded to 1024), through the C ABI
 N > 1 is launched with torch.distributed.run: every rank reduces its own cube
 (independent problems, no collective on the data path), the elapsed time is
 the max over ranks and the value counts the frames of all ranks.
+
+Other workloads (--workload): small (32 x 128^2 reduce), uneven (48 cubes of
+mixed sizes through the batch executors and the autotuner), serve (the
+serving loop alone), precision (512 x 1024^2 shift + rotation per
+arithmetic, tensor-core variants), prep (master skies, sky subtraction, bad
+pixels), register (centroid + Moffat fit of 2000 raw frames), photometry
+(the inject / recentre / bin / reduce / aperture protocol).  --impl
+reference times the CPU oracle on the host cores.
 """
 from __future__ import annotations
 
