@@ -663,3 +663,73 @@ def test_aperture_counts_lattice_points_and_sums():
     ramp = (xx + 2 * yy).astype(np.float32)
     cnt = float(((xx - 20) ** 2 + (yy - 30) ** 2 <= 36).sum())
     assert oracle.aperture(ramp, [20.0], [30.0], 6.0)[0] == cnt * (20 + 60)
+
+
+def test_centroid_patch_is_the_8_connected_component():
+    """The centroid's patch against scipy.ndimage.label (8-connectivity) on
+    the box around the brightest pixel: same size, same flux-weighted
+    centre, and the box-edge / size rules applied to that component."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(62)
+    checked = 0
+    for trial in range(40):
+        N = 48
+        f = rng.normal(0.0, 1.0, (N, N)).astype(np.float32)
+        # a few blobs of random shape, one clearly brightest
+        for _ in range(4):
+            y, x = rng.integers(4, N - 4, 2)
+            f[y - 2:y + 3, x - 2:x + 3] += rng.uniform(2.0, 6.0) * (rng.random((5, 5)) > 0.3)
+        f[rng.integers(8, N - 8), rng.integers(8, N - 8)] += 20.0
+        thresh, R = 1.5, int(rng.integers(3, 12))
+        ok, cx, cy, sz = oracle.centroid(f, thresh, R, 1, 10 ** 6)
+        r0, c0 = np.unravel_index(int(np.argmax(f)), f.shape)
+        rlo, rhi, clo, chi = max(r0 - R, 0), min(r0 + R, N - 1), max(c0 - R, 0), min(c0 + R, N - 1)
+        box = f[rlo:rhi + 1, clo:chi + 1].astype(np.float64)
+        lab, _ = ndimage.label(box > thresh, structure=np.ones((3, 3), int))
+        comp = lab == lab[r0 - rlo, c0 - clo]
+        assert sz == int(comp.sum())
+        H, W = comp.shape
+        touches = ((comp[0].any() and rlo > 0) or (comp[-1].any() and rhi < N - 1) or
+                   (comp[:, 0].any() and clo > 0) or (comp[:, -1].any() and chi < N - 1))
+        assert ok == (not touches)
+        if ok:
+            yy, xx = np.mgrid[rlo:rhi + 1, clo:chi + 1]
+            w = box * comp
+            assert abs(cx - (w * xx).sum() / w.sum()) < 1e-9 and abs(cy - (w * yy).sum() / w.sum()) < 1e-9
+            checked += 1
+    assert checked >= 10
+
+
+def test_moffat_fit_is_a_stationary_point_on_noisy_data():
+    """On a noisy star the fitted parameters zero the gradient of the
+    squared error, computed here by central differences of a numpy model
+    (independent of the oracle's analytic Jacobian): a wrong derivative
+    would stop the iteration at a point where this gradient is not zero."""
+    rng = np.random.default_rng(63)
+    N, w = 64, 10
+    img = _moffat_image(N, 4e4, 31.3, 30.6, 3.2, 2.8, 20.0)
+    img = (img + rng.normal(0.0, 5.0, img.shape)).astype(np.float32)
+    ok, cx, cy, sz = oracle.centroid(img, 200.0, 16, 4, 400)
+    assert ok
+    p, it = oracle.moffat_fit(img, cx, cy, max(1.0, math.sqrt(sz / math.pi)), w)
+    assert it < 200
+    rc, cc = int(math.floor(cy + 0.5)), int(math.floor(cx + 0.5))
+    yy, xx = np.mgrid[rc - w:rc + w + 1, cc - w:cc + w + 1].astype(np.float64)
+    v = img[rc - w:rc + w + 1, cc - w:cc + w + 1].astype(np.float64)
+
+    def cost(q):
+        I0, x0, y0, al, be, bg = q
+        m = I0 * (be - 1) / (math.pi * al * al) * (1 + ((xx - x0) ** 2 + (yy - y0) ** 2) / (al * al)) ** (-be) + bg
+        return float(((m - v) ** 2).sum())
+
+    c0 = cost(p)
+    for k in range(6):
+        h = 1e-5 * max(1.0, abs(p[k]))
+        qp, qm = p.copy(), p.copy()
+        qp[k] += h
+        qm[k] -= h
+        g = (cost(qp) - cost(qm)) / (2 * h)
+        curv = (cost(qp) - 2 * c0 + cost(qm)) / (h * h)
+        # the gradient is zero to the step the curvature allows: |g| / curv << h-scale
+        assert abs(g) <= 1e-6 * c0 / max(1.0, abs(p[k])) + 1e-3 * abs(curv) * h, (k, g, curv)
+    assert abs(p[1] - 31.3) < 0.1 and abs(p[2] - 30.6) < 0.1
