@@ -133,6 +133,23 @@ def kernel_work(kind, n, T):
     return "hbm", n * n * 4, "B"   # collapse: read the cube once
 
 
+def line_pass_roofline(kernels, n, T):
+    """FP32 roofline of the five Fourier line passes together: nominal FFT
+    flops of all frames over the passes' summed device time per step."""
+    kinds = [k for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2", "rot_pass3") if k in kernels]
+    if not kinds:
+        return None
+    flops = T * sum(fft_flops_per_frame(k, n) for k in kinds)
+    ms = sum(kernels[k]["ms_per_step"] for k in kinds)
+    if ms <= 0:
+        return None
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "flops_per_step": flops, "ms_per_step": ms,
+            "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
+            "kernels": kinds}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -386,6 +403,7 @@ def run_gpu(args, rank, world, local_rank):
     step_s = statistics.median(step_ms) / 1e3
     whole = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / step_s / 1e9,
              "frac_of_hbm": alg_bytes / step_s / 1e9 / hbm_peak}
+    line_fp32 = line_pass_roofline(kernels, n, T)
     srt = sorted(step_ms)
     p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
     line = {
@@ -398,6 +416,7 @@ def run_gpu(args, rank, world, local_rank):
                    "parallelism": f"{world} independent cubes (one per GPU)"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "roofline": roof,
+        "line_passes_fp32": line_fp32,
         "whole_step_hbm": whole,
         "kernels": kernels,
         "gpu_launches": int(round(sum(k["launches_per_step"] for k in kernels.values()) * args.steps)),
