@@ -117,3 +117,19 @@ def test_binding_structures_match_the_c_layout(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_rejects_host_tensors_for_the_new_calls():
+    """The Python binding refuses tensors that are not contiguous CUDA
+    float32 cubes / images before reaching the library (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    from paper_1510_04331_gb300 import graphic
+    ctx = graphic.Context.__new__(graphic.Context)   # no device context: the checks come first
+    cube = torch.zeros((2, 64, 64))
+    for call in (lambda: graphic.Context.graphic_register(ctx, cube, 1.0, 8, 3, 400, 6),
+                 lambda: graphic.Context.graphic_bin_median(ctx, cube, 2),
+                 lambda: graphic.Context.graphic_inject(ctx, cube, [0, 0], [32, 32], [32, 32], [5.0], [0.0], [1.0],
+                                                        [2.0, 2.0], [3.0, 3.0], 4),
+                 lambda: graphic.Context.graphic_aperture(ctx, cube[0], [1.0], [1.0], 2.0)):
+        with pytest.raises(graphic.GraphicError):
+            call()
