@@ -733,3 +733,50 @@ def test_moffat_fit_is_a_stationary_point_on_noisy_data():
         # the gradient is zero to the step the curvature allows: |g| / curv << h-scale
         assert abs(g) <= 1e-6 * c0 / max(1.0, abs(p[k])) + 1e-3 * abs(curv) * h, (k, g, curv)
     assert abs(p[1] - 31.3) < 0.1 and abs(p[2] - 30.6) < 0.1
+
+
+# --------------------------------------------------------------------------
+# Exact boundaries of the strict inequalities and tie rules (readings R19,
+# R23, R24, R26): values placed exactly on the boundary, all exactly
+# representable, so "<" against "<=" (or ">" against ">=") decides.
+# --------------------------------------------------------------------------
+
+def test_time_gate_boundary_is_strict():
+    """|t_k - t_i| < t_max: a frame exactly t_max away is outside the set."""
+    T = 9
+    pa = np.linspace(0.0, 80.0, T)                  # every other frame passes the angle gate
+    times = np.arange(T, dtype=np.float64)          # integer hours: differences exact
+    m = oracle.gate_mask(pa, 4, 0.5, times=times, t_max=2.0)
+    assert not m[2] and not m[6]                     # exactly 2 h away: excluded
+    assert m[3] and m[5] and not m[4]                # 1 h away: included; the frame itself: not
+    assert m.sum() == 2
+
+
+def test_sky_subtract_tie_takes_the_earlier_sky():
+    """A frame exactly halfway between two master skies takes the first."""
+    cube = np.zeros((1, 8, 8), np.float32)
+    skies = np.stack([np.full((8, 8), 1.0, np.float32), np.full((8, 8), 2.0, np.float32)])
+    out = oracle.sky_subtract(cube, skies, [1.5], [1.0, 2.0])
+    assert np.all(out == -1.0)
+    out = oracle.sky_subtract(cube, skies[::-1].copy(), [1.5], [2.0, 1.0])   # the first listed sky wins
+    assert np.all(out == -2.0)
+
+
+def test_bad_pixel_map_boundary_is_strict():
+    """|v - median| > C sigma: values of +-1 have median 0 and sigma 1
+    exactly, so at C = 1 no pixel is flagged and at C slightly below 1 all."""
+    ref = np.where((np.arange(16).reshape(4, 4) % 2) == 0, -1.0, 1.0).astype(np.float32)
+    assert not oracle.bad_pixel_map(ref, 1.0).any()
+    assert oracle.bad_pixel_map(ref, 0.999).all()
+
+
+def test_centroid_threshold_is_strict():
+    """Pixels equal to the threshold are below it: a seed equal to it is not
+    found, and a neighbour equal to it stays out of the patch."""
+    f = np.zeros((32, 32), np.float32)
+    f[10, 10] = 8.0
+    f[10, 11] = 4.0
+    f[11, 10] = 5.0
+    ok, cx, cy, sz = oracle.centroid(f, 4.0, 5, 1, 10)
+    assert ok and sz == 2 and cx == 10.0 and cy == (10 * 8.0 + 11 * 5.0) / 13.0
+    assert not oracle.centroid(f, 8.0, 5, 1, 10)[0]
