@@ -780,3 +780,12 @@ def test_centroid_threshold_is_strict():
     ok, cx, cy, sz = oracle.centroid(f, 4.0, 5, 1, 10)
     assert ok and sz == 2 and cx == 10.0 and cy == (10 * 8.0 + 11 * 5.0) / 13.0
     assert not oracle.centroid(f, 8.0, 5, 1, 10)[0]
+
+
+def test_gate_boundary_is_strict():
+    """|alpha_k - alpha_i| > alpha_min: a frame exactly alpha_min away (the
+    differences below are exact) is outside the reference set (R11)."""
+    amin = oracle.alpha_min_deg(4.0, 1.5, 20.0)
+    pa = np.array([0.0, amin, 2.0 * amin])
+    assert list(oracle.gate_mask(pa, 0, amin)) == [False, False, True]
+    assert list(oracle.gate_mask(pa, 2, amin)) == [True, False, False]
