@@ -789,3 +789,16 @@ def test_gate_boundary_is_strict():
     pa = np.array([0.0, amin, 2.0 * amin])
     assert list(oracle.gate_mask(pa, 0, amin)) == [False, False, True]
     assert list(oracle.gate_mask(pa, 2, amin)) == [True, False, False]
+
+
+def test_sky_median_mask_excludes_only_the_inside():
+    """The star mask drops values strictly inside mask_r (R22): a pixel
+    exactly mask_r from the centre stays in the master sky's median."""
+    T, N = 3, 16
+    c = np.zeros((T, N, N), np.float32)
+    c[:, 5, 8] = [10.0, 20.0, 30.0]                  # pixel (x=8, y=5)
+    c[:, 5, 6] = [10.0, 20.0, 30.0]                  # pixel (x=6, y=5)
+    mx, my = np.array([5.0, 100.0, 100.0]), np.array([5.0, 100.0, 100.0])
+    sky = oracle.sky_median(c, mx, my, 3.0)
+    assert sky[5, 8] == 20.0                         # distance exactly 3: kept in every frame
+    assert sky[5, 6] == 25.0                         # distance 1 in frame 0: masked there

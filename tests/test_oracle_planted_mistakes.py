@@ -71,6 +71,14 @@ CASES = [
      "            double ang = (pa0[j] + parang[t]) * ORACLE_PI / 180.0;",
      "            double ang = (pa0[j] - parang[t]) * ORACLE_PI / 180.0;",
      "inject"),
+    ("bad pixel pass reads this pass's fills (R25)",
+     "                            float w = g[(size_t)ii * N + jj];",
+     "                            float w = f[(size_t)ii * N + jj];",
+     "bad_pixel"),
+    ("star mask includes its rim (R22)",
+     "                if (ddx * ddx + ddy * ddy < mask_r * mask_r) continue;",
+     "                if (ddx * ddx + ddy * ddy <= mask_r * mask_r) continue;",
+     "sky"),
     ("aperture boundary strict (R33)",
      "                if (dx * dx + dy * dy <= radius * radius) s += (double)img[(size_t)row * N + col];",
      "                if (dx * dx + dy * dy < radius * radius) s += (double)img[(size_t)row * N + col];",
