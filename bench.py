@@ -41,8 +41,31 @@ if ROOT not in sys.path:
 METRIC = "frames/s (1024² FFT shift+3-shear derot) & % HBM roofline; p50/p99 latency"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per Blackwell SM (4 partitions x 32)
+FALLBACK_SM_MHZ = 2070.0    # GB300 maximum SM clock
+
+
+def fp32_peak(dev=0):
+    """FP32 CUDA-core peak in TFLOP/s from the device's SM count
+    (cudaDevAttrMultiProcessorCount), 128 FMA lanes per SM, 2 flop per FMA,
+    and the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz).
+    Returns (tflops, description)."""
+    sms = None
+    try:
+        import torch
+        sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    except Exception:
+        pass
+    if not sms:
+        sms = 152
+    mhz = FALLBACK_SM_MHZ
+    try:
+        with open(PEAKS_FILE) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return tf, f"FP32 CUDA cores: {sms} SMs (device attribute) x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz:.0f} MHz"
 
 WORKLOADS = {
     "survey": dict(T=2000, n=512, seed=1,
@@ -144,10 +167,10 @@ def line_pass_roofline(kernels, n, T):
     if ms <= 0:
         return None
     achieved = flops / (ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "flops_per_step": flops, "ms_per_step": ms,
-            "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
-            "kernels": kinds}
+    peak, src = fp32_peak()
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_step": flops, "ms_per_step": ms,
+            "peak_source": src, "kernels": kinds}
 
 
 class ClockSampler:
@@ -233,8 +256,9 @@ def cpu_baseline(d, budget_s=15.0):
     rng = np.random.default_rng(0)
     npix = max(1, nt)
     pix = rng.choice(n * n, npix, replace=False)
+    c64_all = d.cube.astype(np.float64)
     t3 = time.perf_counter()
-    oracle.adi_subtract(d.cube.astype(np.float32), d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix)
+    oracle.adi_subtract(c64_all, d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix)
     t4 = time.perf_counter()
     per_pix_adi = (t4 - t3) / npix
     # scale the pixel sample up if the first round was short
@@ -244,21 +268,22 @@ def cpu_baseline(d, budget_s=15.0):
         if more >= 1:
             pix2 = rng.choice(n * n, more, replace=False)
             t5 = time.perf_counter()
-            oracle.adi_subtract(d.cube.astype(np.float32), d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix2)
+            oracle.adi_subtract(c64_all, d.parang, d.fwhm, d.n_fwhm, d.edges, pixels=pix2)
             t6 = time.perf_counter()
             per_pix_adi = ((t4 - t3) + (t6 - t5)) / (npix + more)
             npix += more
     t7 = time.perf_counter()
     cp = rng.choice(n * n, min(n * n, 4096), replace=False)
-    oracle.collapse_median(d.cube.astype(np.float64), pixels=cp)
+    oracle.collapse_median(c64_all, pixels=cp)
     t8 = time.perf_counter()
     per_pix_col = (t8 - t7) / cp.size
     sec_per_cube = per_frame_geom * T + (per_pix_adi + per_pix_col) * n * n
     return {
         "value": T / sec_per_cube, "unit": "frames/s", "cores": nt, "kind": "oracle",
-        "sample": (f"FP64 oracle on {k} frames (shift + 3-shear rotation, {per_frame_geom:.3f} s/frame), "
-                   f"median PSF subtraction on {npix} pixels x {T} frames ({per_pix_adi:.4f} s/pixel) and "
-                   f"median collapse on {cp.size} pixels, scaled to the {T}x{n}x{n} cube"),
+        "sample": (f"FP64 oracle throughout, extrapolated: shift + 3-shear rotation timed on {k} of {T} frames "
+                   f"({per_frame_geom:.3f} s/frame), median PSF subtraction on {npix} of {n * n} pixels x {T} "
+                   f"frames ({per_pix_adi:.4f} s/pixel) and median collapse on {cp.size} pixels, each scaled "
+                   f"linearly to the whole {T}x{n}x{n} cube"),
         "sec_per_cube": sec_per_cube,
     }
 
@@ -390,9 +415,9 @@ def run_gpu(args, rank, world, local_rank):
                 "algorithmic_per_launch": amount}
     else:
         achieved = amount / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": dom,
-                "peak_source": "FP32 CUDA cores: 152 SM x 128 lanes x 2 flop x 2.07 GHz",
+        fpk, fsrc = fp32_peak(local_rank)
+        roof = {"bound": "alu", "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
+                "frac": achieved / fpk, "traffic": None, "kernel": dom, "peak_source": fsrc,
                 "algorithmic_per_launch": amount}
     mt = MEASURED_TRAFFIC.get((dom, T, n))
     if mt:
@@ -423,10 +448,14 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
     }
+    del cube, work
+    torch.cuda.empty_cache()
     if not args.no_serve and world == 1:
-        del cube, work
-        torch.cuda.empty_cache()
         line["serving"] = run_serving(local_rank, n_req=args.serve_requests, max_active=args.serve_max_active)
+    if not args.no_extra and world == 1:
+        # the uneven-batch and precision workloads, a few steps each, under the same clock
+        line["uneven"] = measure_uneven(local_rank, rank, steps=5, warmup=3, tune=True)
+        line["precision"] = measure_precision(local_rank, rank, steps=5, warmup=3)
     if not args.no_cpu_baseline and world == 1:
         cb = cpu_baseline(d, budget_s=args.ref_budget)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -459,17 +488,17 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s"
 
 
-def run_precision(args, rank, world, local_rank):
+def measure_precision(local_rank, rank, steps, warmup, frames=None):
     """Each step: shift then rotate every frame of a 512 x 1024 x 1024 cube
     (the geometric steps of the reduction at 2048-point lines), once per
     arithmetic; errors of each step against the FP64 oracle on sampled
-    frames of the survey recipe at this size."""
+    frames of the survey recipe at this size.  Returns a dict."""
     import torch
     import oracle
     from paper_1510_04331_gb300 import graphic, synth
 
     torch.cuda.set_device(local_rank)
-    T, n = (args.frames or 512), 1024
+    T, n = (frames or 512), 1024
     gen = torch.Generator(device="cuda").manual_seed(3 + rank)
     cube = torch.randn((T, n, n), generator=gen, device="cuda")
     out = torch.empty_like(cube)
@@ -490,12 +519,12 @@ def run_precision(args, rank, world, local_rank):
             ctx.graphic_shift(cube, dx, dy, out=out)
             ctx.graphic_rotate(out, th, out=out)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         ctx.profile(True)
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -507,10 +536,12 @@ def run_precision(args, rank, world, local_rank):
         ctx.profile(False)
         ctx.close()
         med = statistics.median(ms)
-        kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+        kern = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
                 for k, v in prof.items() if v[1]}
         res[name] = {"ms_p50": med, "frames_per_s": T / (med / 1e3), "kernels": kern}
     clocks = sampler.stop() if sampler else None
+    del cube, out
+    torch.cuda.empty_cache()
     # per-step error against the FP64 oracle on 2 frames of the survey recipe at n = 1024
     d = synth.make_cube(2, n, seed=3, parang=synth.altaz_parang(2), peak=1e5, rho=0.99,
                         edges=synth.default_edges(n))
@@ -534,22 +565,35 @@ def run_precision(args, rank, world, local_rank):
     ach = tc_flops / (res[best_tc]["ms_p50"] / 1e3) / 1e12
     fp32_flops = T * sum(fft_flops_per_frame(k, n) for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2",
                                                                 "rot_pass3"))
-    line = {
-        "metric": "frames/s, 1024x1024 shift + 3-shear rotation (2048-point lines), per arithmetic",
-        "value": res[best_tc]["frames_per_s"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": res[best_tc]["ms_p50"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": best_tc, "data": "synthetic",
-        "config": {"workload": f"{T} frames of 1024x1024 padded to 2048, shift U(-0.5,0.5) px + derotation by "
-                               "alt-az angles; errors on 2 frames of the survey recipe (peak 1e5)",
-                   "frames": T, "n": n, "l2": "inputs larger than L2 (%.1f GB)" % (T * n * n * 4 / 1e9)},
+    fpk, fsrc = fp32_peak(local_rank)
+    return {
+        "frames": T, "n": n, "steps": steps, "warmup": warmup, "best_tensor_core": best_tc,
+        "workload": f"{T} frames of 1024x1024 padded to 2048, shift U(-0.5,0.5) px + derotation by "
+                    "alt-az angles; errors on 2 frames of the survey recipe (peak 1e5)",
         "variants": res,
+        "tensor_vs_fp32_frames_per_s": res[best_tc]["frames_per_s"] / res["fp32"]["frames_per_s"],
         "roofline": {"bound": "tensor", "achieved": ach, "peak": bpk, "unit": "TFLOP/s", "frac": ach / bpk,
                      "traffic": None, "kernel": f"line_pass_tc ({best_tc}), GEMM flops executed",
                      "peak_source": bsrc, "algorithmic_per_launch": tc_flops},
         "fp32_roofline": {"bound": "alu", "achieved": fp32_flops / (res["fp32"]["ms_p50"] / 1e3) / 1e12,
-                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                          "frac": fp32_flops / (res["fp32"]["ms_p50"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS},
+                          "peak": fpk, "unit": "TFLOP/s", "peak_source": fsrc,
+                          "frac": fp32_flops / (res["fp32"]["ms_p50"] / 1e3) / 1e12 / fpk},
         "clocks": clocks,
+    }
+
+
+def run_precision(args, rank, world, local_rank):
+    r = measure_precision(local_rank, rank, args.steps, args.warmup, args.frames)
+    best = r["best_tensor_core"]
+    line = {
+        "metric": "frames/s, 1024x1024 shift + 3-shear rotation (2048-point lines), per arithmetic",
+        "value": r["variants"][best]["frames_per_s"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["variants"][best]["ms_p50"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": best, "data": "synthetic",
+        "config": {"workload": r["workload"], "frames": r["frames"], "n": r["n"],
+                   "l2": "inputs larger than L2 (%.1f GB)" % (r["frames"] * r["n"] ** 2 * 4 / 1e9)},
+        "variants": r["variants"], "roofline": r["roofline"], "fp32_roofline": r["fp32_roofline"],
+        "clocks": r["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -966,7 +1010,10 @@ def run_serving(local_rank, n_req=200, rates=(20.0, 200.0, 2000.0), seed=4, max_
 # uneven batches: 48 cubes, sides 64..1024, 16..400 frames, shift + rotation
 # ---------------------------------------------------------------------------
 
-def run_uneven(args, rank, world, local_rank):
+def measure_uneven(local_rank, rank, steps, warmup, tune=True):
+    """The 48-cube uneven batch (shift + rotation of every frame) through
+    the per-cube, persistent and grouped executors, after the autotuner
+    (unless tune is False).  Returns a dict."""
     import torch
     from paper_1510_04331_gb300 import graphic, synth
 
@@ -981,18 +1028,20 @@ def run_uneven(args, rank, world, local_rank):
     frames = sum(sp[1] for sp in spec)
     ctx = graphic.Context(local_rank)
     tuned = None
-    if not args.no_tune:
+    if tune:
+        t0 = time.perf_counter()
         sched, t_pc, t_ps, t_gr = ctx.graphic_autotune(cubes, dx, dy, th, outs=outs)
-        tuned = {"schedule": sched, "best_per_cube_ms": t_pc, "best_persistent_ms": t_ps, "best_grouped_ms": t_gr}
+        tuned = {"schedule": sched, "best_per_cube_ms": t_pc, "best_persistent_ms": t_ps, "best_grouped_ms": t_gr,
+                 "tuning_s": time.perf_counter() - t0}
     res = {}
     modes = ((graphic.BATCH_PER_CUBE, "per_cube"), (graphic.BATCH_PERSISTENT, "persistent"),
              (graphic.BATCH_GROUPED, "grouped"))
     for mode, name in modes:
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ctx.graphic_batch_geom(cubes, dx, dy, th, outs=outs, mode=mode)
         torch.cuda.synchronize()
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -1002,27 +1051,44 @@ def run_uneven(args, rank, world, local_rank):
             ms.append(e0.elapsed_time(e1))
         res[name] = {"ms_p50": statistics.median(ms), "frames_per_s": frames / (statistics.median(ms) / 1e3)}
     batched = "grouped" if ctx.schedule()["batch_mode"] == graphic.BATCH_GROUPED else "persistent"
+    ctx.close()
+    nbytes = sum(c.numel() for c in cubes) * 4
+    del cubes, outs
+    torch.cuda.empty_cache()
     # algorithmic flops of the batch (nominal 5 m log2 m per complex line transform, both ways)
     flops = 0.0
     for (n, T, _, _, _) in spec:
         flops += T * sum(fft_flops_per_frame(k, n) for k in ("shift_x", "shift_y", "rot_pass1", "rot_pass2",
                                                               "rot_pass3"))
     bs = res[batched]["ms_p50"] / 1e3
-    line = {
-        "metric": "frames/s, uneven batch (shift + 3-shear rotation)", "value": res[batched]["frames_per_s"],
-        "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res[batched]["ms_p50"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "48 cubes, sides from {64,128,256,512,1024}, 16-400 frames each (seeded), shifts "
-                               "U(-2,2) px, rotations U(0,360) deg", "frames": frames,
-                   "sides": [sp[0] for sp in spec], "counts": [sp[1] for sp in spec],
-                   "l2": "inputs larger than L2 (%.1f GB)" % (sum(c.numel() for c in cubes) * 4 / 1e9)},
+    fpk, fsrc = fp32_peak(local_rank)
+    return {
+        "workload": "48 cubes, sides from {64,128,256,512,1024}, 16-400 frames each (seeded), shifts "
+                    "U(-2,2) px, rotations U(0,360) deg", "frames": frames, "steps": steps, "warmup": warmup,
+        "sides": [sp[0] for sp in spec], "counts": [sp[1] for sp in spec], "input_bytes": nbytes,
         "batched_mode": batched, "modes": res,
         "speedup_batched_vs_per_cube": res["per_cube"]["ms_p50"] / res[batched]["ms_p50"],
+        "speedup_persistent_vs_per_cube": res["per_cube"]["ms_p50"] / res["persistent"]["ms_p50"],
         "autotune": tuned,
-        "roofline": {"bound": "alu", "achieved": flops / bs / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / bs / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "batch_" + batched,
-                     "algorithmic_per_launch": flops},
+        "roofline": {"bound": "alu", "achieved": flops / bs / 1e12, "peak": fpk, "unit": "TFLOP/s",
+                     "frac": flops / bs / 1e12 / fpk, "traffic": None, "kernel": "batch_" + batched,
+                     "peak_source": fsrc, "algorithmic_per_launch": flops},
+    }
+
+
+def run_uneven(args, rank, world, local_rank):
+    r = measure_uneven(local_rank, rank, args.steps, args.warmup, tune=not args.no_tune)
+    b = r["batched_mode"]
+    line = {
+        "metric": "frames/s, uneven batch (shift + 3-shear rotation)", "value": r["modes"][b]["frames_per_s"],
+        "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["modes"][b]["ms_p50"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "frames": r["frames"], "sides": r["sides"], "counts": r["counts"],
+                   "l2": "inputs larger than L2 (%.1f GB)" % (r["input_bytes"] / 1e9)},
+        "batched_mode": b, "modes": r["modes"],
+        "speedup_batched_vs_per_cube": r["speedup_batched_vs_per_cube"],
+        "autotune": r["autotune"], "roofline": r["roofline"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1045,6 +1111,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0, help="seconds of oracle work per sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uneven-batch and precision sub-measurements of the default line")
     ap.add_argument("--t-max", type=float, default=None,
                     help="time gate of the median PSF: reference frames within this many hours")
     ap.add_argument("--serve-requests", type=int, default=200)

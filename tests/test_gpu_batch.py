@@ -162,3 +162,90 @@ def test_batch_rejects_bad_passes_and_modes(g, batch):
     with pytest.raises(g.GraphicError):
         ctx.set_schedule(group_streams=9)
     ctx.close()
+
+
+# --------------------------------------------------------------------------
+# Every executor and schedule against the FP64 oracle (shift, Sect. 3.3.1,
+# then the three-shear rotation, Sect. 3.4), not only against the library's
+# own per-call passes.
+# --------------------------------------------------------------------------
+
+def _oracle_batch():
+    """Cubes of every supported side, one of 40 frames, with the angles of
+    each cube spread over the four quarter turns (theta = 90 q + theta',
+    q = 0..3) where its frame count allows, and all four present at every
+    side taken together with the other cubes of that side."""
+    rng = np.random.default_rng(2024)
+    spec = [(64, 40), (128, 6), (256, 4), (512, 3), (1024, 2), (1024, 2), (512, 2), (64, 5)]
+    out = []
+    for k, (n, T) in enumerate(spec):
+        cube = synth.random_frames(T, n, seed=100 + k)
+        cube += synth.random_frames(T, n, seed=200 + k, smooth=True) * 50.0
+        dx = rng.uniform(-2, 2, T)
+        dy = rng.uniform(-2, 2, T)
+        q = (np.arange(T) + 2 * (k % 2)) % 4              # quarter turns cycling 0..3
+        th = 90.0 * q + rng.uniform(-44.9, 44.9, T)
+        out.append((cube.astype(np.float32), dx, dy, th))
+    return out
+
+
+@pytest.fixture(scope="module")
+def oracle_batch():
+    import oracle
+    b = _oracle_batch()
+    ref = [oracle.rotate(oracle.shift(c.astype(np.float64), dx, dy), th) for c, dx, dy, th in b]
+    return b, ref
+
+
+def test_oracle_batch_covers_sizes_and_quarter_turns():
+    b = _oracle_batch()
+    sides = {c.shape[1] for c, _, _, _ in b}
+    assert sides == {64, 128, 256, 512, 1024}
+    assert max(c.shape[0] for c, _, _, _ in b) >= 32
+    for n in sides:
+        qs = set()
+        for c, _, _, th in b:
+            if c.shape[1] == n:
+                qs |= {int(np.floor(t / 90.0 + 0.5)) % 4 for t in th}
+        assert qs == {0, 1, 2, 3}, (n, qs)
+
+
+@pytest.mark.parametrize("variant_1024", [0, 1])
+@pytest.mark.parametrize("mode", [PER_CUBE, PERSISTENT, GROUPED])
+def test_batch_executors_match_fp64_oracle(g, oracle_batch, mode, variant_1024):
+    """Each executor (per-cube, persistent single launch, grouped graph) under
+    both 1024-point line kernels (generic radix-16, radix-32 warp kernel)
+    equals oracle.shift then oracle.rotate within 1e-5 of each cube's input
+    peak, element by element, on two calls in a row (the second replays the
+    recorded graph)."""
+    b, ref = oracle_batch
+    ctx = g.Context(0)
+    ctx.set_schedule(variant_1024=variant_1024)
+    cubes = [torch.from_numpy(c).cuda() for c, _, _, _ in b]
+    for rep in range(2):
+        outs = ctx.graphic_batch_geom(cubes, *_args(b), mode=mode)
+        for o, r, (c, _, _, _) in zip(outs, ref, b):
+            err = np.abs(o.cpu().numpy().astype(np.float64) - r).max()
+            assert err <= 1e-5 * np.abs(c).max(), (c.shape, err / np.abs(c).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant_1024", [0, 1])
+def test_per_call_1024_kernels_match_fp64_oracle(g, oracle_batch, variant_1024):
+    """graphic_shift and graphic_rotate on 1024 x 1024 frames, each step
+    against its own oracle step, with either 1024-point line kernel."""
+    import oracle
+    b, _ = oracle_batch
+    ctx = g.Context(0)
+    ctx.set_schedule(variant_1024=variant_1024)
+    for c, dx, dy, th in b:
+        if c.shape[1] not in (512, 1024):
+            continue
+        s = ctx.graphic_shift(torch.from_numpy(c).cuda(), dx, dy)
+        ref_s = oracle.shift(c.astype(np.float64), dx, dy)
+        assert np.abs(s.cpu().numpy() - ref_s).max() <= 1e-5 * np.abs(c).max()
+        s32 = s.cpu().numpy()
+        r = ctx.graphic_rotate(s, th)
+        ref_r = oracle.rotate(s32.astype(np.float64), th)
+        assert np.abs(r.cpu().numpy() - ref_r).max() <= 1e-5 * np.abs(s32).max()
+    ctx.close()

@@ -55,3 +55,31 @@ def test_rotate_noalloc_matches_rotate_on_two_calls():
     c = torch.zeros((2, 96, 96), device="cuda")
     assert _noalloc(lib, c, [1.0, 2.0], c) == -2
     assert b"n must be" in lib.graphic_last_error()
+
+
+def test_rotate_noalloc_matches_fp64_oracle_at_512_and_1024():
+    """Against the FP64 oracle's three-shear rotation (Sect. 3.4) on the two
+    largest sides, with ragged last chunks of the static scratch: 9 frames of
+    512 x 512 (chunks of 8 + 1, the radix-32 warp kernel) and then 5 frames of
+    1024 x 1024 (chunks of 2 + 2 + 1), two calls in a row."""
+    import oracle
+    from paper_1510_04331_gb300 import graphic
+    lib = graphic.lib()
+    rng = np.random.default_rng(77)
+    cases = []
+    for T, n, seed in ((9, 512, 21), (5, 1024, 22)):
+        f = synth.random_frames(T, n, seed=seed) + 40.0 * synth.random_frames(T, n, seed=seed + 1, smooth=True)
+        th = rng.uniform(-180, 180, T)
+        th[:4] = [-170.0, -80.0, 11.3, 135.0]              # all four quarter turns
+        cases.append((f.astype(np.float32), th))
+    outs = []
+    for f, th in cases:
+        x = torch.from_numpy(f).cuda()
+        out = torch.full_like(x, float("nan"))
+        assert _noalloc(lib, x, th, out) == 0, lib.graphic_last_error()
+        outs.append(out)
+    torch.cuda.synchronize()
+    for (f, th), out in zip(cases, outs):
+        ref = oracle.rotate(f.astype(np.float64), th)
+        err = np.abs(out.cpu().numpy().astype(np.float64) - ref).max()
+        assert err <= TOL * np.abs(f).max(), (f.shape, err / np.abs(f).max())
