@@ -118,12 +118,7 @@ def job_throughput(units_per_rank_step, steps, world, max_ms):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of a whole step of
 # one kernel, from ncu captures of the current kernels: (kernel, frames, n) ->
 # (bytes per step at that size, source).  Per launch = bytes / launches.
-MEASURED_TRAFFIC = {
-    ("adi_median", 2000, 512): (
-        3.619e9,
-        "ncu dram bytes of the median PSF launches (general + band) at 200 frames of the survey recipe "
-        "(361.9 MB), scaled x10 to 2000 frames (traffic grows with the frames)"),
-}
+MEASURED_TRAFFIC = {}
 
 
 def peaks():
@@ -151,8 +146,10 @@ def kernel_work(kind, n, T):
     """(bound, algorithmic amount per launch-frame, unit) for one frame."""
     if kind in ("shift_x", "shift_y", "rot_pass1", "rot_pass2", "rot_pass3"):
         return "alu", fft_flops_per_frame(kind, n), "flop"
-    if kind == "adi_median":
-        return "hbm", 2 * n * n * 4, "B"
+    if kind in ("adi_band_sweep", "adi_general"):
+        return "hbm", 2 * n * n * 4, "B"   # reads the cube, writes the residuals
+    if kind == "adi_band_prep":
+        return "hbm", n * n * 4, "B"       # reads the cube
     return "hbm", n * n * 4, "B"   # collapse: read the cube once
 
 

@@ -73,6 +73,24 @@ const char *graphic_last_error(void);
 int graphic_version(void);
 
 /*
+ * A cube in device memory with a frame stride, for cubes that are views into
+ * larger buffers (a sub-range of frames of a bigger allocation, frames
+ * padded to an alignment): frame t starts at data + t * frame_stride floats.
+ * frame_stride == 0 means n*n (dense); otherwise frame_stride >= n*n and a
+ * multiple of 4, so that every frame starts on a 16-byte boundary
+ * (GRAPHIC_ERR_INVALID_ARG otherwise).  data is owned by the caller.  The
+ * *_cube calls below are the plain calls with this description of their
+ * cubes; the floats between frames are neither read nor written.
+ */
+typedef struct {
+  float *data;           /* device pointer to frame 0 */
+  int64_t n_frames;
+  int32_t n;
+  int32_t reserved_;     /* zero */
+  int64_t frame_stride;  /* elements between frames, 0 = n*n */
+} graphic_cube;
+
+/*
  * Sub-pixel recentring shift (Sect. 3.3.1, shift theorem with the separable
  * 2-D phasor, on frames zero-padded to m = 2n).  Frame t is moved by
  * (dx[t], dy[t]) pixels: out(x, y) = in(x - dx, y - dy), computed as a row
@@ -124,6 +142,18 @@ int graphic_adi_subtract(graphic_ctx *ctx, const float *in, float *out, int64_t 
 int graphic_collapse_median(graphic_ctx *ctx, const float *in, int64_t n_frames, int32_t n, float *out);
 
 /*
+ * The four steps above on strided cubes (graphic_cube).  in and out must have
+ * the same n and n_frames; in-place calls pass the same cube twice.
+ */
+int graphic_shift_cube(graphic_ctx *ctx, const graphic_cube *in, const graphic_cube *out, const double *dx,
+                       const double *dy);
+int graphic_rotate_cube(graphic_ctx *ctx, const graphic_cube *in, const graphic_cube *out, const double *theta_deg);
+int graphic_adi_subtract_cube(graphic_ctx *ctx, const graphic_cube *in, const graphic_cube *out,
+                              const double *parang_deg, double fwhm, double n_fwhm, const double *annuli_edges,
+                              int32_t n_edges);
+int graphic_collapse_median_cube(graphic_ctx *ctx, const graphic_cube *in, float *out);
+
+/*
  * The whole reduction (Sect. 3, PSF subtraction then derotation and merge):
  * shift by (dx, dy) from `in` into `work`, median PSF subtraction in place in
  * `work`, derotation by theta = -parang in place in `work`, median collapse
@@ -133,6 +163,12 @@ int graphic_collapse_median(graphic_ctx *ctx, const float *in, int64_t n_frames,
 int graphic_reduce(graphic_ctx *ctx, const float *in, float *work, int64_t n_frames, int32_t n,
                    const double *dx, const double *dy, const double *parang_deg, double fwhm, double n_fwhm,
                    const double *annuli_edges, int32_t n_edges, float *out);
+
+/* graphic_reduce on strided cubes: in is only read, work (same n and
+ * n_frames, its own stride) holds the intermediate frames, out is n*n. */
+int graphic_reduce_cube(graphic_ctx *ctx, const graphic_cube *in, const graphic_cube *work, const double *dx,
+                        const double *dy, const double *parang_deg, double fwhm, double n_fwhm,
+                        const double *annuli_edges, int32_t n_edges, float *out);
 
 /*
  * The same two calls with the paper's second reference-frame condition
@@ -418,7 +454,9 @@ int graphic_get_precision(graphic_ctx *ctx, int32_t *precision);
 #define GRAPHIC_K_REG_ARGMAX 8
 #define GRAPHIC_K_REG_FIT 9
 #define GRAPHIC_K_BIN 10
-#define GRAPHIC_K_COUNT 11
+#define GRAPHIC_K_ADI_BAND_PREP 11
+#define GRAPHIC_K_ADI_BAND_SWEEP 12
+#define GRAPHIC_K_COUNT 13
 
 /* enable != 0: bracket every kernel launch of the context with CUDA events
  * on its stream and accumulate per-kernel device time and launch counts;
@@ -427,9 +465,11 @@ int graphic_profile(graphic_ctx *ctx, int enable);
 
 /* Copy the accumulated device milliseconds and launch counts of the first
  * n kernels (ids above) into ms[] and launches[] (host arrays of n).  The
- * median PSF step is one bracketed interval of 1 to 3 kernel launches
- * (general path, band paths); launches[] counts the kernels, and a grouped
- * or persistent batch call (GRAPHIC_K_BATCH) counts as one graph launch. */
+ * median PSF step is up to three kinds of interval: its general path
+ * (GRAPHIC_K_ADI_MEDIAN, named "adi_general"), the band path's preparation
+ * kernels (with the kernel that zeroes groups outside the annuli) and its
+ * sweep kernels, one launch of each per bit-map width class; a grouped or
+ * persistent batch call (GRAPHIC_K_BATCH) counts as one graph launch. */
 int graphic_profile_read(graphic_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
 /* Name of kernel id `k` (static string), NULL if out of range. */

@@ -48,6 +48,8 @@ struct graphic_ctx {
   size_t cube_bytes = 0;
   float *d_img = nullptr;           // graphic_reduce_host device result
   size_t img_bytes = 0;
+  char *d_bscratch = nullptr;       // median PSF band path: per-pixel band tables
+  size_t bscratch_bytes = 0;
   bool prof = false;
   double prof_ms[GRAPHIC_K_COUNT] = {};
   int64_t prof_n[GRAPHIC_K_COUNT] = {};
@@ -260,27 +262,31 @@ int graphic::validate_shift(const double *dx, const double *dy, int64_t T, int32
 namespace {
 
 // Enqueue the two shift passes for frames [0, T) with parameters at device
-// pointers p_dx, p_dy.  in -> out (out may equal in).
+// pointers p_dx, p_dy.  in -> out (out may equal in); in_fs / out_fs: the
+// frame strides in elements (0: n*n).
 int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *p_dx,
-                  const double *p_dy) {
+                  const double *p_dy, long long in_fs = 0, long long out_fs = 0) {
   const long long NN = (long long)n * n;
+  if (!in_fs) in_fs = NN;
+  if (!out_fs) out_fs = NN;
   const long long ch = chunk_frames(c, T, (size_t)NN * sizeof(float));
   for (long long f0 = 0; f0 < T; f0 += ch) {
     const long long nf = std::min<long long>(ch, T - f0);
     LineArgs a{};
-    a.in = in + f0 * NN;
-    a.out = out + f0 * NN;
+    a.in = in + f0 * in_fs;
+    a.out = out + f0 * out_fs;
     a.p0 = p_dx + f0;
     a.p1 = p_dy + f0;
     a.status = c->d_status;
-    a.in_fstride = NN;
-    a.out_fstride = NN;
+    a.in_fstride = in_fs;
+    a.out_fstride = out_fs;
     a.n = n;
     prof_begin(c, GRAPHIC_K_SHIFT_X);
     cudaError_t e = line_pass(c, SHIFT_X, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift x pass");
-    a.in = out + f0 * NN;
+    a.in = out + f0 * out_fs;
+    a.in_fstride = out_fs;
     prof_begin(c, GRAPHIC_K_SHIFT_Y);
     e = line_pass(c, SHIFT_Y, a, nf, c->stream);
     prof_end(c);
@@ -318,9 +324,11 @@ int plan_rotate(const double *theta, int64_t T, bool negate, RotPlanHost &rp) {
 }
 
 int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const double *p_a,
-                   const double *p_s, const int *p_q) {
+                   const double *p_s, const int *p_q, long long in_fs = 0, long long out_fs = 0) {
   const long long NN = (long long)n * n;
   const long long NM = NN * 2;
+  if (!in_fs) in_fs = NN;
+  if (!out_fs) out_fs = NN;
   const long long ch = chunk_frames(c, T, (size_t)NM * sizeof(float));
   int rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, (size_t)ch * NM * sizeof(float), false);
   if (rc) return rc;
@@ -333,9 +341,9 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.status = c->d_status;
     a.n = n;
     // pass 1: frame rows (after rot90^q) -> scratch rows of 2n
-    a.in = in + f0 * NN;
+    a.in = in + f0 * in_fs;
     a.out = c->d_scratch;
-    a.in_fstride = NN;
+    a.in_fstride = in_fs;
     a.out_fstride = NM;
     prof_begin(c, GRAPHIC_K_ROT_P1);
     cudaError_t e = line_pass(c, ROT_P1, a, nf, c->stream);
@@ -351,8 +359,8 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "rotation pass 2");
     // pass 3: scratch rows -> frame rows
-    a.out = out + f0 * NN;
-    a.out_fstride = NN;
+    a.out = out + f0 * out_fs;
+    a.out_fstride = out_fs;
     prof_begin(c, GRAPHIC_K_ROT_P3);
     e = line_pass(c, ROT_P3, a, nf, c->stream);
     prof_end(c);
@@ -525,10 +533,35 @@ int graphic::plan_adi(const double *parang, int64_t T, double fwhm, double n_fwh
 
 namespace {
 
-int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
-                const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann,
-                const int *p_ab = nullptr) {
+// Plan tables of the median PSF step in the uploaded plan (byte offsets).
+struct AdiOffsets {
+  size_t perm, lr, e2, band, ab, evq, groups;
+};
+
+AdiOffsets add_adi_plan(PlanBuilder &pb, const AdiPlanHost &ap, int64_t T) {
+  AdiOffsets o{};
+  o.e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
+  o.perm = pb.add(ap.perm.data(), T * sizeof(int));
+  o.lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
+  o.band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
+  o.ab = pb.add(ap.ab.data(), ap.ab.size() * sizeof(int));
+  o.evq = pb.add(ap.evq.data(), ap.evq.size() * sizeof(uint32_t));
+  o.groups = pb.add(ap.groups.data(), ap.groups.size() * sizeof(int));
+  return o;
+}
+
+int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
+                    const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann,
+                    const int *p_ab, const uint32_t *p_evq, const int *p_groups, const std::vector<int> &class_off,
+                    char *band_scratch, size_t band_scratch_cap, long long in_fs, long long out_fs) {
   AdiArgs a{};
+  a.in_fs = in_fs ? in_fs : (long long)n * n;
+  a.out_fs = out_fs ? out_fs : (long long)n * n;
+  a.band_scratch_cap = band_scratch_cap;
+  a.evq = p_evq;
+  a.groups = p_groups;
+  for (int k = 0; k < 8; k++) a.class_off[k] = k < (int)class_off.size() ? class_off[k] : 0;
+  a.band_scratch = band_scratch;
   a.in = in;
   a.out = out;
   a.perm = p_perm;
@@ -541,17 +574,25 @@ int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t 
   a.T = (int)T;
   a.n = n;
   a.n_ann = n_ann;
-  prof_begin(c, GRAPHIC_K_ADI_MEDIAN);
+  // profiling: one bracket per group of launches (general path, band
+  // preparation with the zero groups, band sweep)
+  a.mark_user = c;
+  a.mark = [](void *u, int kind, int begin) {
+    graphic_ctx *cc = static_cast<graphic_ctx *>(u);
+    const int id = kind == 0 ? GRAPHIC_K_ADI_MEDIAN : kind == 1 ? GRAPHIC_K_ADI_BAND_PREP : GRAPHIC_K_ADI_BAND_SWEEP;
+    if (begin) prof_begin(cc, id);
+    else prof_end(cc);
+  };
   int launched = 0;
   cudaError_t e = launch_adi_median(a, c->stream, &launched);
-  prof_end(c);
-  if (c->prof && launched > 1) c->prof_extra[GRAPHIC_K_ADI_MEDIAN] += launched - 1;
   if (e != cudaSuccess) return cuda_fail(e, "median PSF kernel");
   return GRAPHIC_OK;
 }
 
-int enqueue_collapse(graphic_ctx *c, const float *in, int64_t T, int32_t n, float *out) {
+
+int enqueue_collapse(graphic_ctx *c, const float *in, int64_t T, int32_t n, float *out, long long in_fs = 0) {
   CollapseArgs a{};
+  a.fs = in_fs;
   a.in = in;
   a.out = out;
   a.status = c->d_status;
@@ -569,13 +610,26 @@ const T *at(const graphic_ctx *c, size_t off) {
   return reinterpret_cast<const T *>(c->d_plan + off);
 }
 
+int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const AdiPlanHost &ap,
+                const AdiOffsets &o, long long in_fs = 0, long long out_fs = 0) {
+  const size_t need = band_scratch_bytes(ap, T);
+  if (need) {
+    int rc = ensure((void **)&c->d_bscratch, &c->bscratch_bytes, need, false);
+    if (rc) return rc;
+  }
+  return enqueue_adi_raw(c, in, out, T, n, at<int>(c, o.perm), at<int>(c, o.lr), at<double>(c, o.e2),
+                         at<int>(c, o.band), ap.wmax, (int)ap.edge2.size() - 1,
+                         ap.ab.empty() ? nullptr : at<int>(c, o.ab), at<uint32_t>(c, o.evq), at<int>(c, o.groups),
+                         ap.class_off, c->d_bscratch, c->bscratch_bytes, in_fs, out_fs);
+}
+
 // Full reduction of the device cube `in` (work may equal in).  With host_in,
 // `in` is first filled from host_in, chunk by chunk on the context's copy
 // stream, each chunk's shift pass starting as soon as its copy is done.
 int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32_t n, const double *dx,
                   const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
                   int32_t n_edges, float *out, const float *host_in = nullptr, const double *times = nullptr,
-                  double t_max = 0.0) {
+                  double t_max = 0.0, long long in_fs = 0, long long work_fs = 0) {
   int rc = validate_shift(dx, dy, T, n);
   if (rc) return rc;
   rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges);
@@ -585,21 +639,18 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
   if (rc) return rc;
   AdiPlanHost ap;
   if ((rc = plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap, times, t_max))) return rc;
+  if ((rc = plan_band_path(ap, T, n))) return rc;
   PlanBuilder pb;
   const size_t o_dx = pb.add(dx, T * sizeof(double));
   const size_t o_dy = pb.add(dy, T * sizeof(double));
   const size_t o_a = pb.add(rp.a.data(), T * sizeof(double));
   const size_t o_s = pb.add(rp.s.data(), T * sizeof(double));
-  const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
   const size_t o_q = pb.add(rp.q.data(), T * sizeof(int));
-  const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
-  const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
-  const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
-  const size_t o_ab = pb.add(ap.ab.data(), ap.ab.size() * sizeof(int));
+  const AdiOffsets oa = add_adi_plan(pb, ap, T);
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
   if (!host_in) {
-    if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy)))) return rc;
+    if ((rc = enqueue_shift(c, in, work, T, n, at<double>(c, o_dx), at<double>(c, o_dy), in_fs, work_fs))) return rc;
   } else {
     if (!c->s_copy) {
       CK(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
@@ -624,11 +675,11 @@ int reduce_device(graphic_ctx *c, const float *in, float *work, int64_t T, int32
         return rc;
     }
   }
-  if ((rc = enqueue_adi(c, work, work, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
-                        at<int>(c, o_band), ap.wmax, n_edges - 1, ap.ab.empty() ? nullptr : at<int>(c, o_ab))))
+  if ((rc = enqueue_adi(c, work, work, T, n, ap, oa, work_fs, work_fs))) return rc;
+  if ((rc = enqueue_rotate(c, work, work, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q), work_fs,
+                           work_fs)))
     return rc;
-  if ((rc = enqueue_rotate(c, work, work, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q)))) return rc;
-  if ((rc = enqueue_collapse(c, work, T, n, out))) return rc;
+  if ((rc = enqueue_collapse(c, work, T, n, out, work_fs))) return rc;
   return GRAPHIC_OK;
 }
 
@@ -1231,6 +1282,9 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_scratch);
   cudaFree(c->d_cube);
   cudaFree(c->d_img);
+  cudaFree(c->d_bscratch);
+  c->d_bscratch = nullptr;
+  c->bscratch_bytes = 0;
   cudaFree(c->d_counters);
   cudaFree(c->d_gscratch);
   c->d_gscratch = nullptr;
@@ -1321,18 +1375,13 @@ int graphic_adi_subtract_ex(graphic_ctx *c, const float *in, float *out, int64_t
   if ((rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges))) return rc;
   AdiPlanHost ap;
   if ((rc = plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap, times, t_max))) return rc;
+  if ((rc = plan_band_path(ap, T, n))) return rc;
   DeviceGuard g(c->device);
   PlanBuilder pb;
-  const size_t o_e2 = pb.add(ap.edge2.data(), ap.edge2.size() * sizeof(double));
-  const size_t o_perm = pb.add(ap.perm.data(), T * sizeof(int));
-  const size_t o_lr = pb.add(ap.lr.data(), ap.lr.size() * sizeof(int));
-  const size_t o_band = pb.add(ap.band.data(), ap.band.size() * sizeof(int));
-  const size_t o_ab = pb.add(ap.ab.data(), ap.ab.size() * sizeof(int));
+  const AdiOffsets oa = add_adi_plan(pb, ap, T);
   if ((rc = begin_call(c))) return rc;
   if ((rc = upload_plan(c, pb))) return rc;
-  if ((rc = enqueue_adi(c, in, out, T, n, at<int>(c, o_perm), at<int>(c, o_lr), at<double>(c, o_e2),
-                        at<int>(c, o_band), ap.wmax, n_edges - 1, ap.ab.empty() ? nullptr : at<int>(c, o_ab))))
-    return rc;
+  if ((rc = enqueue_adi(c, in, out, T, n, ap, oa))) return rc;
   return end_call(c);
 }
 
@@ -1393,6 +1442,123 @@ int graphic_reduce_host(graphic_ctx *c, const float *host_in, int64_t T, int32_t
     return rc;
   }
   CK(cudaMemcpyAsync(host_out, c->d_img, NN * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return end_call(c);
+}
+
+// --- strided cubes ------------------------------------------------------------
+namespace {
+int check_cube_desc(const graphic_cube *cb, const char *what, long long &fs) {
+  if (!cb) return fail(GRAPHIC_ERR_INVALID_ARG, std::string("null ") + what + " cube");
+  const long long NN = (long long)cb->n * cb->n;
+  fs = cb->frame_stride ? cb->frame_stride : NN;
+  if (cb->frame_stride && (cb->frame_stride < NN || (cb->frame_stride & 3)))
+    return fail(GRAPHIC_ERR_INVALID_ARG, std::string(what) + ": frame_stride must be 0 or >= n*n and a multiple of 4");
+  return GRAPHIC_OK;
+}
+int check_pair(const graphic_cube *in, const graphic_cube *out, long long &ifs, long long &ofs) {
+  int rc = check_cube_desc(in, "in", ifs);
+  if (rc) return rc;
+  if ((rc = check_cube_desc(out, "out", ofs))) return rc;
+  if (in->n != out->n || in->n_frames != out->n_frames)
+    return fail(GRAPHIC_ERR_INVALID_ARG, "in and out cubes differ in n or n_frames");
+  return check_cube(in->data, out->data, in->n_frames, in->n);
+}
+}  // namespace
+
+int graphic_shift_cube(graphic_ctx *c, const graphic_cube *in, const graphic_cube *out, const double *dx,
+                       const double *dy) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  long long ifs, ofs;
+  int rc = check_pair(in, out, ifs, ofs);
+  if (rc) return rc;
+  const int64_t T = in->n_frames;
+  const int32_t n = in->n;
+  if ((rc = validate_shift(dx, dy, T, n))) return rc;
+  if (T == 0) return GRAPHIC_OK;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_dx = pb.add(dx, T * sizeof(double));
+  const size_t o_dy = pb.add(dy, T * sizeof(double));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_shift(c, in->data, out->data, T, n, at<double>(c, o_dx), at<double>(c, o_dy), ifs, ofs)))
+    return rc;
+  return end_call(c);
+}
+
+int graphic_rotate_cube(graphic_ctx *c, const graphic_cube *in, const graphic_cube *out, const double *theta) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  long long ifs, ofs;
+  int rc = check_pair(in, out, ifs, ofs);
+  if (rc) return rc;
+  const int64_t T = in->n_frames;
+  const int32_t n = in->n;
+  if (T > 0 && !theta) return fail(GRAPHIC_ERR_INVALID_ARG, "null theta");
+  if (T == 0) return GRAPHIC_OK;
+  RotPlanHost rp;
+  if ((rc = plan_rotate(theta, T, false, rp))) return rc;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const size_t o_a = pb.add(rp.a.data(), T * sizeof(double));
+  const size_t o_s = pb.add(rp.s.data(), T * sizeof(double));
+  const size_t o_q = pb.add(rp.q.data(), T * sizeof(int));
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_rotate(c, in->data, out->data, T, n, at<double>(c, o_a), at<double>(c, o_s), at<int>(c, o_q),
+                           ifs, ofs)))
+    return rc;
+  return end_call(c);
+}
+
+int graphic_adi_subtract_cube(graphic_ctx *c, const graphic_cube *in, const graphic_cube *out, const double *parang,
+                              double fwhm, double n_fwhm, const double *edges, int32_t n_edges) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  long long ifs, ofs;
+  int rc = check_pair(in, out, ifs, ofs);
+  if (rc) return rc;
+  const int64_t T = in->n_frames;
+  const int32_t n = in->n;
+  if ((rc = validate_adi(parang, T, fwhm, n_fwhm, edges, n_edges))) return rc;
+  AdiPlanHost ap;
+  if ((rc = plan_adi(parang, T, fwhm, n_fwhm, edges, n_edges, ap))) return rc;
+  if ((rc = plan_band_path(ap, T, n))) return rc;
+  DeviceGuard g(c->device);
+  PlanBuilder pb;
+  const AdiOffsets oa = add_adi_plan(pb, ap, T);
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = upload_plan(c, pb))) return rc;
+  if ((rc = enqueue_adi(c, in->data, out->data, T, n, ap, oa, ifs, ofs))) return rc;
+  return end_call(c);
+}
+
+int graphic_collapse_median_cube(graphic_ctx *c, const graphic_cube *in, float *out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  long long ifs;
+  int rc = check_cube_desc(in, "in", ifs);
+  if (rc) return rc;
+  if ((rc = check_cube(in->data, out, in->n_frames, in->n))) return rc;
+  if (in->n_frames < 1) return fail(GRAPHIC_ERR_INVALID_ARG, "n_frames < 1");
+  DeviceGuard g(c->device);
+  if ((rc = begin_call(c))) return rc;
+  if ((rc = enqueue_collapse(c, in->data, in->n_frames, in->n, out, ifs))) return rc;
+  return end_call(c);
+}
+
+int graphic_reduce_cube(graphic_ctx *c, const graphic_cube *in, const graphic_cube *work, const double *dx,
+                        const double *dy, const double *parang, double fwhm, double n_fwhm, const double *edges,
+                        int32_t n_edges, float *out) {
+  if (!c) return fail(GRAPHIC_ERR_INVALID_ARG, "null ctx");
+  long long ifs, wfs;
+  int rc = check_pair(in, work, ifs, wfs);
+  if (rc) return rc;
+  if (!out) return fail(GRAPHIC_ERR_INVALID_ARG, "null out");
+  DeviceGuard g(c->device);
+  if ((rc = reduce_device(c, in->data, work->data, in->n_frames, in->n, dx, dy, parang, fwhm, n_fwhm, edges, n_edges,
+                          out, nullptr, nullptr, 0.0, ifs, wfs))) {
+    cudaStreamSynchronize(c->stream);
+    c->ev_used = 0;
+    return rc;
+  }
   return end_call(c);
 }
 
@@ -1850,16 +2016,17 @@ int graphic_profile_read(graphic_ctx *c, double *ms, int64_t *launches, int32_t 
 }
 
 const char *graphic_kernel_name(int32_t k) {
-  static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_median", "rot_pass1",
+  static const char *names[GRAPHIC_K_COUNT] = {"shift_x", "shift_y", "adi_general", "rot_pass1",
                                               "rot_pass2", "rot_pass3", "collapse_median", "batch_persistent",
-                                              "register_argmax", "register_fit", "bin_median"};
+                                              "register_argmax", "register_fit", "bin_median", "adi_band_prep",
+                                              "adi_band_sweep"};
   return (k >= 0 && k < GRAPHIC_K_COUNT) ? names[k] : nullptr;
 }
 
 int graphic_workspace_bytes(graphic_ctx *c, int64_t *bytes) {
   if (!c || !bytes) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
   *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->gscratch_bytes + c->cube_bytes + c->img_bytes +
-                     c->counters_bytes);
+                     c->counters_bytes + c->bscratch_bytes);
   return GRAPHIC_OK;
 }
 

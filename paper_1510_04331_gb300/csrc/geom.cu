@@ -40,6 +40,10 @@ namespace {
 // stored back to back at offset m - 128 (FP64 cos/sin rounded to FP32).
 constexpr int kTwTotal = 4096 - 128;
 __device__ float2 d_twiddle[kTwTotal];
+// The twiddles of the radix-32 x 32 warp FFT (m = 1024), W_1024^(r lane) at
+// [r][lane] (the same values as d_twiddle): lane-contiguous, so each of the
+// 31 twiddle loads of a lane group is one coalesced 256-byte access.
+__device__ float2 d_tw1024_rl[32 * 32];
 
 __host__ __device__ constexpr int tw_off(int m) { return m - 128; }
 
@@ -516,7 +520,7 @@ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
 // Two radix-32 Stockham stages over the 1024-point line held as v[m] =
 // element lane + 32 m: after the call v[r] = X[lane + 32 r].  buf: the warp's
-// exchange buffer (1024 + 32 entries).
+// exchange buffer (1024 + 32 entries); tw: W_1024^(r lane) at [r][lane].
 __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *buf,
                                              const float2 *__restrict__ tw) {
   dft32(v);
@@ -526,7 +530,7 @@ __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *
 #pragma unroll
   for (int m = 0; m < 32; m++) v[m] = buf[pad32(lane + 32 * m)];
 #pragma unroll
-  for (int r = 1; r < 32; r++) v[r] = cmul(v[r], __ldg(&tw[r * lane]));
+  for (int r = 1; r < 32; r++) v[r] = cmul(v[r], __ldg(&tw[r * 32 + lane]));
   dft32(v);
   __syncwarp();
 }
@@ -548,7 +552,7 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
   const int line0 = 2 * (blockIdx.x * PPC + p);
   const float *__restrict__ fin = a.in_tab ? a.in_tab[f] : a.in + f * a.in_fstride;
   float *__restrict__ fout = a.out_tab ? a.out_tab[f] : a.out + f * a.out_fstride;
-  const float2 *__restrict__ tw = d_twiddle + tw_off(M);
+  const float2 *__restrict__ tw = d_tw1024_rl;
   float2 *buf = sbuf[p];
   const int q = (KIND == ROT_P1) ? (a.q[f] & 3) : 0;
 
@@ -956,6 +960,10 @@ int geom_init_device() {
       }
     filled = true;
   }
+  static float2 rl[32 * 32];
+  for (int r = 0; r < 32; r++)
+    for (int l = 0; l < 32; l++) rl[r * 32 + l] = host[tw_off(1024) + r * l];
+  if (cudaMemcpyToSymbol(d_tw1024_rl, rl, sizeof(rl)) != cudaSuccess) return -1;
   return cudaMemcpyToSymbol(d_twiddle, host, sizeof(host)) == cudaSuccess ? 0 : -1;
 }
 

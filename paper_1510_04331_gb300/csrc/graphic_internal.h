@@ -56,11 +56,26 @@ struct AdiPlanHost {
   std::vector<double> edge2; // [A+1]
   std::vector<int> band;     // [A][4]
   int wmax = 0;
+  // band path (plan_band_path): event queries [A][T] (a_s | b_s << 16: frame s
+  // is outside the reference set of the queries a_s <= i < b_s), the 4-pixel
+  // groups of the band path class after class (0: no pixel in an annulus;
+  // then bit map widths 1, 2, 4, 8, 16, 32 words), class offsets [8]
+  std::vector<uint32_t> evq;
+  std::vector<int> groups;
+  std::vector<int> class_off;
 };
 // Returns GRAPHIC_OK, or an error code (last error set) for times that are
 // not monotone in the angle order or a t_max that is not > 0.
 int plan_adi(const double *parang, int64_t T, double fwhm, double n_fwhm, const double *edges, int32_t n_edges,
              AdiPlanHost &ap, const double *times = nullptr, double t_max = 0.0);
+// Band path tables of a plan for frames of side n (psf_band.cu); the groups
+// of a geometry are cached.  band_scratch_bytes: the device scratch the band
+// path of that plan needs.
+int plan_band_path(AdiPlanHost &ap, int64_t T, int32_t n);
+size_t band_scratch_bytes(const AdiPlanHost &ap, int64_t T);
+// The band path works through its pixel groups in chunks whose tables fit
+// the scratch it is given; kBandScratchMax bounds what callers allocate.
+constexpr size_t kBandScratchMax = (size_t)256 << 20;
 
 // Asynchronous context calls for the serving loop (capi.cu): a batch call on
 // the context's stream without the final synchronisation (the status word is
@@ -142,14 +157,30 @@ struct AdiArgs {
   const int *band;       // [A][4] (blo, bhi, W, 0): full-rank band holding every median the
                          // annulus needs, W = bitmap words per lane (0: general path)
   int *status;
+  long long in_fs;       // elements between consecutive frames of in (n*n for dense cubes)
+  long long out_fs;      // elements between consecutive frames of out
   int T;
   int n;
   int n_ann;             // A
   int wmax;              // largest W over the annuli (0: no band path)
+  // band path (psf_band.cu), from plan_band_path
+  const uint32_t *evq;   // [A][T] device
+  const int *groups;     // device, class after class
+  int class_off[8];      // host copy of AdiPlanHost::class_off
+  char *band_scratch;    // device scratch of band_scratch_cap bytes (at least one group's tables)
+  size_t band_scratch_cap;
+  // optional hook around each group of launches (profiling): mark(user,
+  // kind, 1) before and mark(user, kind, 0) after; kind 0 = general path,
+  // 1 = band preparation (and the zero groups), 2 = band sweep
+  void (*mark)(void *user, int kind, int begin);
+  void *mark_user;
 };
 // *launched (may be null) receives the number of kernels launched (1 to 3:
 // general path, band path W <= 16, band path W = 32).
 cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched = nullptr);
+// psf_band.cu: the band path's launches (zero groups, then per class the
+// preparation and the sweep); *launched is incremented per kernel
+cudaError_t launch_adi_band(const AdiArgs &a, cudaStream_t st, int *launched);
 
 struct CollapseArgs {
   const float *in;
@@ -157,6 +188,7 @@ struct CollapseArgs {
   int *status;
   long long T;
   int n;
+  long long fs;          // elements between consecutive frames of in (0: n*n)
   // master-sky variant (launch_sky_median): values that are not finite or
   // lie within mask_r of the frame's (mask_x[t], mask_y[t]) are left out
   const double *mask_x;  // [T] device, may be null (no mask)

@@ -109,9 +109,10 @@ struct Req {
   graphic::AdiPlanHost ap;
   int n_ann = 0;
   // device arena: cube, result, plan
-  size_t cube_bytes = 0, out_bytes = 0, plan_bytes = 0;
+  // (plan_dev_bytes: the plan's device region, the staged tables)
+  size_t cube_bytes = 0, out_bytes = 0, plan_bytes = 0, plan_dev_bytes = 0;
   size_t off_cube = Arena::kNone, off_out = Arena::kNone, off_plan = Arena::kNone;
-  size_t o_perm = 0, o_lr = 0, o_e2 = 0, o_band = 0;   // within the plan
+  size_t o_perm = 0, o_lr = 0, o_e2 = 0, o_band = 0, o_evq = 0, o_groups = 0;   // within the plan
   // pinned staging: plan copy-in, result copy-out
   size_t stage_bytes = 0, off_stage = Arena::kNone;
   int slot = -1;   // per-request device status word
@@ -138,6 +139,7 @@ struct graphic_server {
   Clock::time_point t0;
   char *d_arena = nullptr;
   Arena arena;
+  char *d_band = nullptr;   // median PSF band path tables (kBandScratchMax), shared by the requests
   char *h_stage = nullptr;
   Arena stage;
   int *d_status = nullptr;     // [max_active]
@@ -200,7 +202,7 @@ void fail_req(Req *r, int code, const std::string &msg) {
 void retire(graphic_server *s, Req *r) {
   if (r->off_cube != Arena::kNone) s->arena.release(r->off_cube, r->cube_bytes);
   if (r->off_out != Arena::kNone) s->arena.release(r->off_out, r->out_bytes);
-  if (r->off_plan != Arena::kNone) s->arena.release(r->off_plan, r->plan_bytes);
+  if (r->off_plan != Arena::kNone) s->arena.release(r->off_plan, r->plan_dev_bytes);
   if (r->off_stage != Arena::kNone) s->stage.release(r->off_stage, r->stage_bytes);
   r->off_cube = r->off_out = r->off_plan = r->off_stage = Arena::kNone;
   if (r->slot >= 0) s->free_slots.push_back(r->slot);
@@ -259,6 +261,8 @@ int start_copy_in(graphic_server *s, Req *r) {
   memcpy(hp + r->o_lr, r->ap.lr.data(), r->ap.lr.size() * sizeof(int));
   memcpy(hp + r->o_e2, r->ap.edge2.data(), r->ap.edge2.size() * sizeof(double));
   memcpy(hp + r->o_band, r->ap.band.data(), r->ap.band.size() * sizeof(int));
+  memcpy(hp + r->o_evq, r->ap.evq.data(), r->ap.evq.size() * sizeof(uint32_t));
+  memcpy(hp + r->o_groups, r->ap.groups.data(), r->ap.groups.size() * sizeof(int));
   cudaError_t e = cudaMemcpyAsync(s->d_arena + r->off_plan, hp, r->plan_bytes, cudaMemcpyHostToDevice, s->s_in);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status + r->slot, 0, sizeof(int), s->s_in);
   if (e == cudaSuccess)
@@ -279,7 +283,7 @@ void admit(graphic_server *s) {
       if (s->queue.empty()) return;
       r = s->queue.front();
     }
-    const size_t need = Arena::round(r->cube_bytes) + Arena::round(r->out_bytes) + Arena::round(r->plan_bytes);
+    const size_t need = Arena::round(r->cube_bytes) + Arena::round(r->out_bytes) + Arena::round(r->plan_dev_bytes);
     if (need > s->arena.cap() || Arena::round(r->stage_bytes) > s->stage.cap()) {
       {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -292,13 +296,13 @@ void admit(graphic_server *s) {
     if (s->free_slots.empty()) return;
     r->off_cube = s->arena.alloc(r->cube_bytes);
     if (r->off_cube != Arena::kNone) r->off_out = s->arena.alloc(r->out_bytes);
-    if (r->off_out != Arena::kNone) r->off_plan = s->arena.alloc(r->plan_bytes);
+    if (r->off_out != Arena::kNone) r->off_plan = s->arena.alloc(r->plan_dev_bytes);
     if (r->off_plan != Arena::kNone) r->off_stage = s->stage.alloc(r->stage_bytes);
     if (r->off_stage == Arena::kNone) {
       // does not fit yet: give back what was taken, wait for completions
       if (r->off_cube != Arena::kNone) s->arena.release(r->off_cube, r->cube_bytes);
       if (r->off_out != Arena::kNone) s->arena.release(r->off_out, r->out_bytes);
-      if (r->off_plan != Arena::kNone) s->arena.release(r->off_plan, r->plan_bytes);
+      if (r->off_plan != Arena::kNone) s->arena.release(r->off_plan, r->plan_dev_bytes);
       r->off_cube = r->off_out = r->off_plan = Arena::kNone;
       return;
     }
@@ -412,9 +416,15 @@ void issue_iteration(graphic_server *s) {
     a.edge2 = reinterpret_cast<const double *>(plan + r->o_e2);
     a.band = reinterpret_cast<const int *>(plan + r->o_band);
     a.wmax = r->ap.wmax;
+    a.evq = reinterpret_cast<const uint32_t *>(plan + r->o_evq);
+    a.groups = reinterpret_cast<const int *>(plan + r->o_groups);
+    for (int k = 0; k < 8; k++) a.class_off[k] = k < (int)r->ap.class_off.size() ? r->ap.class_off[k] : 0;
+    a.band_scratch = s->d_band;   // shared: the median launches run one after the other on s_comp
+    a.band_scratch_cap = graphic::kBandScratchMax;
     a.status = s->d_status + r->slot;
     a.T = (int)r->T;
     a.n = r->n;
+    a.in_fs = a.out_fs = (long long)r->n * r->n;
     a.n_ann = r->n_ann;
     if (graphic::launch_adi_median(a, s->s_comp) != cudaSuccess) fail_req(r, GRAPHIC_ERR_CUDA, "median PSF kernel");
   }
@@ -525,7 +535,7 @@ int graphic_server_create(graphic_server **out, const graphic_server_config *cfg
     return graphic::set_last_error(GRAPHIC_ERR_CUDA, cudaGetErrorString(e));
   }
   // budget: the asked bytes, at most free HBM minus both contexts' workspaces and a margin
-  const size_t ws = 2 * graphic::ctx_workspace_bound(s->ctx[0], mode) + ((size_t)1 << 30);
+  const size_t ws = 2 * graphic::ctx_workspace_bound(s->ctx[0], mode) + ((size_t)1 << 30) + graphic::kBandScratchMax;
   size_t budget = c.max_device_bytes ? (size_t)c.max_device_bytes : ((size_t)150 << 30);
   budget = std::min(budget, free_b > ws ? free_b - ws : 0);
   budget &= ~(Arena::kAlign - 1);
@@ -535,6 +545,7 @@ int graphic_server_create(graphic_server **out, const graphic_server_config *cfg
   }
   const size_t staging = c.staging_bytes ? (size_t)c.staging_bytes : ((size_t)256 << 20);
   e = cudaMalloc(&s->d_arena, budget);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_band, graphic::kBandScratchMax);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_stage, staging);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int) * s->max_active);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_status, sizeof(int) * s->max_active);
@@ -567,7 +578,8 @@ int graphic_server_submit(graphic_server *s, const graphic_request *rq, int64_t 
   r->dy.assign(rq->dy, rq->dy + T);
   r->theta.resize(T);
   for (int64_t t = 0; t < T; t++) r->theta[t] = -rq->parang[t];
-  if ((rc = graphic::plan_adi(rq->parang, T, rq->fwhm, rq->n_fwhm, rq->edges, rq->n_edges, r->ap))) {
+  if ((rc = graphic::plan_adi(rq->parang, T, rq->fwhm, rq->n_fwhm, rq->edges, rq->n_edges, r->ap)) ||
+      (rc = graphic::plan_band_path(r->ap, T, rq->n))) {
     delete r;
     return rc;
   }
@@ -584,7 +596,12 @@ int graphic_server_submit(graphic_server *s, const graphic_request *rq, int64_t 
   o = align16(o + r->ap.edge2.size() * sizeof(double));
   r->o_band = o;
   o = align16(o + r->ap.band.size() * sizeof(int));
+  r->o_evq = o;
+  o = align16(o + r->ap.evq.size() * sizeof(uint32_t));
+  r->o_groups = o;
+  o = align16(o + r->ap.groups.size() * sizeof(int));
   r->plan_bytes = o;
+  r->plan_dev_bytes = o;
   r->stage_bytes = r->plan_bytes + r->out_bytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {
@@ -657,6 +674,7 @@ int graphic_server_destroy(graphic_server *s) {
   for (int k = 0; k < 2; k++)
     if (s->ctx[k]) graphic_destroy(s->ctx[k]);
   cudaFree(s->d_arena);
+  cudaFree(s->d_band);
   cudaFreeHost(s->h_stage);
   cudaFree(s->d_status);
   cudaFreeHost(s->h_status);

@@ -30,8 +30,8 @@ ERRORS = {
     -6: "GRAPHIC_ERR_TIMEOUT",
     -7: "GRAPHIC_ERR_INTERNAL",
 }
-KERNELS = ["shift_x", "shift_y", "adi_median", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median",
-           "batch_persistent", "register_argmax", "register_fit", "bin_median"]
+KERNELS = ["shift_x", "shift_y", "adi_general", "rot_pass1", "rot_pass2", "rot_pass3", "collapse_median",
+           "batch_persistent", "register_argmax", "register_fit", "bin_median", "adi_band_prep", "adi_band_sweep"]
 BATCH_PER_CUBE = 0
 BATCH_PERSISTENT = 1
 BATCH_GROUPED = 2
@@ -52,6 +52,12 @@ class BatchItem(ctypes.Structure):
                 ("dx", ctypes.POINTER(ctypes.c_double)), ("dy", ctypes.POINTER(ctypes.c_double)),
                 ("theta_deg", ctypes.POINTER(ctypes.c_double))]
 MAX_FRAMES_MEDIAN = 2048
+
+
+class Cube(ctypes.Structure):
+    """graphic_cube of include/graphic.h: a device cube with a frame stride."""
+    _fields_ = [("data", ctypes.c_void_p), ("n_frames", ctypes.c_int64), ("n", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("frame_stride", ctypes.c_int64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -142,6 +148,13 @@ _SIGS = {
     "graphic_autotune": [_P, _P, _I32, ctypes.c_char_p, _D],
     "graphic_get_schedule": [_P, ctypes.POINTER(_I32), _I32],
     "graphic_set_schedule": [_P, ctypes.POINTER(_I32), _I32],
+    "graphic_shift_cube": [_P, ctypes.POINTER(Cube), ctypes.POINTER(Cube), _D, _D],
+    "graphic_rotate_cube": [_P, ctypes.POINTER(Cube), ctypes.POINTER(Cube), _D],
+    "graphic_adi_subtract_cube": [_P, ctypes.POINTER(Cube), ctypes.POINTER(Cube), _D, ctypes.c_double,
+                                  ctypes.c_double, _D, _I32],
+    "graphic_collapse_median_cube": [_P, ctypes.POINTER(Cube), _P],
+    "graphic_reduce_cube": [_P, ctypes.POINTER(Cube), ctypes.POINTER(Cube), _D, _D, _D, ctypes.c_double,
+                            ctypes.c_double, _D, _I32, _P],
 }
 
 
@@ -185,6 +198,16 @@ def _cube(t, name="cube"):
     return t
 
 
+def _strided(t, name="cube"):
+    """graphic_cube of a CUDA float32 tensor (T, n, n) whose rows and columns
+    are dense and whose frames are frame_stride = t.stride(0) floats apart."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 3
+            and t.shape[1] == t.shape[2] and t.stride(2) == 1 and t.stride(1) == t.shape[2]):
+        raise GraphicError(-1, f"{name} must be a CUDA float32 (T, n, n) tensor with dense frames")
+    return Cube(t.data_ptr(), t.shape[0], t.shape[1], 0, t.stride(0))
+
+
 class Context:
     """A library context bound to one CUDA device (owns its workspaces)."""
 
@@ -219,6 +242,55 @@ class Context:
         dya, pdy = _f64(dy, T)
         self._stream()
         _check(lib().graphic_shift(self.h, _P(cube.data_ptr()), _P(out.data_ptr()), T, n, pdx, pdy))
+        return out
+
+    # --- strided cubes (graphic_cube): views whose frames are not adjacent ---
+    def graphic_shift_cube(self, cube, dx, dy, out):
+        ci, co = _strided(cube), _strided(out, "out")
+        T = cube.shape[0]
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        self._stream()
+        _check(lib().graphic_shift_cube(self.h, ctypes.byref(ci), ctypes.byref(co), pdx, pdy))
+        return out
+
+    def graphic_rotate_cube(self, cube, theta_deg, out):
+        ci, co = _strided(cube), _strided(out, "out")
+        tha, pth = _f64(theta_deg, cube.shape[0])
+        self._stream()
+        _check(lib().graphic_rotate_cube(self.h, ctypes.byref(ci), ctypes.byref(co), pth))
+        return out
+
+    def graphic_adi_subtract_cube(self, cube, parang, fwhm, n_fwhm, edges, out):
+        ci, co = _strided(cube), _strided(out, "out")
+        paa, ppa = _f64(parang, cube.shape[0])
+        e = np.ascontiguousarray(edges, np.float64)
+        self._stream()
+        _check(lib().graphic_adi_subtract_cube(self.h, ctypes.byref(ci), ctypes.byref(co), ppa, float(fwhm),
+                                               float(n_fwhm), e.ctypes.data_as(_D), e.size))
+        return out
+
+    def graphic_collapse_median_cube(self, cube, out=None):
+        import torch
+        ci = _strided(cube)
+        n = cube.shape[1]
+        out = torch.empty((n, n), dtype=torch.float32, device=cube.device) if out is None else out
+        self._stream()
+        _check(lib().graphic_collapse_median_cube(self.h, ctypes.byref(ci), _P(out.data_ptr())))
+        return out
+
+    def graphic_reduce_cube(self, cube, dx, dy, parang, fwhm, n_fwhm, edges, work, out=None):
+        import torch
+        ci, cw = _strided(cube), _strided(work, "work")
+        T, n = cube.shape[0], cube.shape[1]
+        out = torch.empty((n, n), dtype=torch.float32, device=cube.device) if out is None else out
+        dxa, pdx = _f64(dx, T)
+        dya, pdy = _f64(dy, T)
+        paa, ppa = _f64(parang, T)
+        e = np.ascontiguousarray(edges, np.float64)
+        self._stream()
+        _check(lib().graphic_reduce_cube(self.h, ctypes.byref(ci), ctypes.byref(cw), pdx, pdy, ppa, float(fwhm),
+                                         float(n_fwhm), e.ctypes.data_as(_D), e.size, _P(out.data_ptr())))
         return out
 
     def graphic_rotate(self, cube, theta_deg, out=None):

@@ -33,8 +33,28 @@ def lib():
 def test_header_declares_the_path():
     names = declared_functions()
     for required in ["graphic_shift", "graphic_rotate", "graphic_adi_subtract", "graphic_collapse_median",
-                     "graphic_reduce", "graphic_reduce_host", "graphic_create", "graphic_destroy"]:
+                     "graphic_reduce", "graphic_reduce_host", "graphic_create", "graphic_destroy",
+                     "graphic_shift_cube", "graphic_rotate_cube", "graphic_adi_subtract_cube",
+                     "graphic_collapse_median_cube", "graphic_reduce_cube"]:
         assert required in names
+
+
+def test_strided_cube_calls_check_their_descriptions_without_gpu(lib):
+    """graphic_cube arguments: null descriptions and bad frame strides (below
+    n*n, or not a multiple of 4 floats) are refused on the host."""
+    from paper_1510_04331_gb300 import graphic
+    import ctypes as ct
+    ctx = ct.c_void_p(1)   # never dereferenced: the description checks come first
+    good = graphic.Cube(256, 3, 64, 0, 64 * 64 + 16)
+    for stride in (64 * 64 - 4, 64 * 64 + 2):
+        bad = graphic.Cube(256, 3, 64, 0, stride)
+        assert lib.graphic_shift_cube(ctx, ct.byref(bad), ct.byref(good), None, None) == -1
+        assert b"frame_stride" in lib.graphic_last_error()
+        assert lib.graphic_collapse_median_cube(ctx, ct.byref(bad), ct.c_void_p(256)) == -1
+    other = graphic.Cube(256, 4, 64, 0, 0)
+    assert lib.graphic_rotate_cube(ctx, ct.byref(good), ct.byref(other), None) == -1
+    assert b"differ" in lib.graphic_last_error()
+    assert lib.graphic_reduce_cube(ctx, None, ct.byref(good), None, None, None, 4.0, 1.5, None, 2, None) == -1
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -99,7 +119,7 @@ def test_binding_structures_match_the_c_layout(tmp_path):
     from paper_1510_04331_gb300 import graphic
     structs = {"graphic_batch_item": graphic.BatchItem, "graphic_server_config": graphic.ServerConfig,
                "graphic_request": graphic.Request, "graphic_request_info": graphic.RequestInfo,
-               "graphic_server_stats": graphic.ServerStats}
+               "graphic_server_stats": graphic.ServerStats, "graphic_cube": graphic.Cube}
     c_names = {"in_": "in"}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "graphic_serve.h"', "int main(void) {"]
     for cname, py in structs.items():
