@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
   uint32_t *kw = keys_all + w;   // key of frame t: kw[t * COL_KS]
   bool bad = false;
   uint32_t kmin = 0xffffffffu, kmax = 0u, orv = 0u, andv = 0xffffffffu;
+#pragma unroll 4
   for (int t = lane; t < T; t += 32) {
     const float v = __uint_as_float(kw[t * COL_KS]);
     bad |= !isfinite(v);
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
 #pragma unroll
   for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0u;
   __syncwarp();
+#pragma unroll 4
   for (int t = lane; t < T; t += 32) atomicAdd(&hist[vbin_c(kw[t * COL_KS], v0, scale)], 1u);
   __syncwarp();
   uint32_t h[8], hs = 0;
@@ -325,14 +327,23 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     uint32_t *cbuf = keys_all + (size_t)w * cap * COL_KS + (COL_KS - 1);   // element j at cbuf[j * COL_KS]
     const unsigned lt = (1u << lane) - 1u;
     int len = 0;
-    for (int t0 = 0; t0 < T; t0 += 32) {
-      const int t = t0 + lane;
-      const uint32_t k = t < T ? kw[t * COL_KS] : 0u;
-      const int b = vbin_c(k, v0, scale);
-      const bool in = t < T && b >= bin[0] && b <= bin[1];
-      const unsigned mm = __ballot_sync(FULL, in);
-      if (in) cbuf[(len + __popc(mm & lt)) * COL_KS] = k;
-      len += __popc(mm);
+    // four 32-frame rounds per step: their loads and bins are independent
+    for (int t0 = 0; t0 < T; t0 += 128) {
+      uint32_t k[4];
+      bool in[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int t = t0 + 32 * u + lane;
+        k[u] = t < T ? kw[t * COL_KS] : 0u;
+        const int b = vbin_c(k[u], v0, scale);
+        in[u] = t < T && b >= bin[0] && b <= bin[1];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const unsigned mm = __ballot_sync(FULL, in[u]);
+        if (in[u]) cbuf[(len + __popc(mm & lt)) * COL_KS] = k[u];
+        len += __popc(mm);
+      }
     }
     __syncwarp();
     // ranks r0, r1 within the list: the key with (#smaller) <= r < (#smaller or equal)

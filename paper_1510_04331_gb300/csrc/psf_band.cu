@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
 #pragma unroll
   for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0u;
   __syncwarp();
+#pragma unroll 4
   for (int s = lane; s < T; s += 32) atomicAdd(&hist[vbin(kw[s * KS], v0, scale)], 1u);
   __syncwarp();
   int B0, B1;
@@ -245,23 +246,33 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
   uint32_t cmin = 0xffffffffu, cmax = 0u;
   __syncwarp();
   if (ncand <= B.cap) {
-    for (int base = 0; base < T; base += 32) {
-      const int s = base + lane;
-      const bool valid = s < T;
-      const uint32_t k = valid ? kw[s * KS] : 0u;
-      const int b = valid ? vbin(k, v0, scale) : 0;
-      const bool isc = valid && b >= B0 && b <= B1;
-      const bool isb = valid && b < B0;
-      const unsigned mc = __ballot_sync(FULL, isc), mb = __ballot_sync(FULL, isb);
-      if (isc) {
-        const int j = nc + __popc(mc & lt);
-        ckey[j] = k;
-        cs[j] = (uint16_t)s;
-        cmin = min(cmin, k);
-        cmax = max(cmax, k);
+    // four 32-frame rounds per step: their loads and bins are independent
+    for (int base = 0; base < T; base += 128) {
+      uint32_t k[4];
+      int b[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int s = base + 32 * u + lane;
+        k[u] = s < T ? kw[s * KS] : 0u;
+        b[u] = s < T ? vbin(k[u], v0, scale) : 256;
       }
-      if (lane == 0) below[base >> 5] = mb;
-      nc += __popc(mc);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int s = base + 32 * u + lane;
+        if (base + 32 * u >= T) break;
+        const bool isc = b[u] >= B0 && b[u] <= B1;
+        const bool isb = b[u] < B0;
+        const unsigned mc = __ballot_sync(FULL, isc), mb = __ballot_sync(FULL, isb);
+        if (isc) {
+          const int j = nc + __popc(mc & lt);
+          ckey[j] = k[u];
+          cs[j] = (uint16_t)s;
+          cmin = min(cmin, k[u]);
+          cmax = max(cmax, k[u]);
+        }
+        if (lane == 0) below[(base >> 5) + u] = mb;
+        nc += __popc(mc);
+      }
     }
     nbelow = (int)bel0;
   } else {
@@ -384,18 +395,18 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
 
 // Shared memory: per warp skeys[NB] u32, blev[NB] u32, bm[NB] u32 (bit map,
 // word wd of lane c at wd * 32 + c), blpos[NB] u16, belowc[nwt + 1] uint2
-// (BELOW word, BELOW frames before it); per CTA the staged gates of up to two
-// annuli [2][T] u32 (L | R << 16) and the value / residual blocks.
+// (BELOW word, BELOW frames before it); per CTA the staged gate of the
+// group's first annulus [T] u32 (L | R << 16) and the value / residual blocks.
 __host__ __device__ inline size_t sweep_warp_bytes(int NB, int nwt) {
   return (size_t)NB * 12 + al16((size_t)NB * 2) + al16((size_t)(nwt + 1) * 8);
 }
 constexpr size_t kBlockBytes = (size_t)SWK * 32 * 16;   // [SWK][32 lanes] float4
 __host__ __device__ inline size_t sweep_smem_bytes(int NB, int nwt, int T) {
-  return PPC * sweep_warp_bytes(NB, nwt) + al16((size_t)2 * T * 4) + 3 * kBlockBytes;
+  return PPC * sweep_warp_bytes(NB, nwt) + al16((size_t)T * 4) + 3 * kBlockBytes;
 }
 
 template <int WC>
-__global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 5 : (WC == 16 ? 4 : 2)) band_sweep_kernel(const BandArgs B) {
+__global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) band_sweep_kernel(const BandArgs B) {
   extern __shared__ __align__(16) unsigned char ssm[];
   constexpr int NB = 32 * WC;
   const AdiArgs &a = B.a;
@@ -410,10 +421,10 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 5 : (WC == 16 ? 4 : 2)) 
   uint16_t *blpos = reinterpret_cast<uint16_t *>(bm + NB);
   uint2 *belowc = reinterpret_cast<uint2 *>(wb + (size_t)NB * 12 + al16((size_t)NB * 2));
   unsigned char *cb_ = ssm + PPC * sweep_warp_bytes(NB, nwt);
-  uint32_t *gate_all = reinterpret_cast<uint32_t *>(cb_);                               // [2][T]
-  float4 *vbuf = reinterpret_cast<float4 *>(cb_ + al16((size_t)2 * T * 4));            // [2][SWK][32]
-  float *obuf = reinterpret_cast<float *>(cb_ + al16((size_t)2 * T * 4) + 2 * kBlockBytes);   // [SWK][32][4]
-  __shared__ int gate_ann[2];
+  uint32_t *gate_all = reinterpret_cast<uint32_t *>(cb_);                               // [T]
+  float4 *vbuf = reinterpret_cast<float4 *>(cb_ + al16((size_t)T * 4));                // [2][SWK][32]
+  float *obuf = reinterpret_cast<float *>(cb_ + al16((size_t)T * 4) + 2 * kBlockBytes);   // [SWK][32][4]
+  __shared__ int gate_ann[1];
 
   // ---- this pixel's band data -------------------------------------------
   const char *slot = B.slots + ((size_t)blockIdx.x * PPC + w) * B.slot_bytes;
@@ -447,28 +458,26 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 5 : (WC == 16 ? 4 : 2)) 
       carry += __shfl_sync(FULL, inc, 31);
     }
   }
-  // ---- gates of the group's annuli (at most two staged) ---------------------
-  if (threadIdx.x < 2) gate_ann[threadIdx.x] = -1;
+  // ---- gate of the group's first annulus, staged ---------------------------
+  if (threadIdx.x == 0) gate_ann[0] = -1;
   __syncthreads();
-  if (lane == 0 && ann >= 0) {
-    if (atomicCAS(&gate_ann[0], -1, ann) != -1 && gate_ann[0] != ann) atomicCAS(&gate_ann[1], -1, ann);
-  }
+  if (lane == 0 && ann >= 0) atomicCAS(&gate_ann[0], -1, ann);
   __syncthreads();
-  for (int g = 0; g < 2; g++) {
-    const int an = gate_ann[g];
-    if (an < 0) continue;
-    const int2 *lr2 = reinterpret_cast<const int2 *>(a.lr + (size_t)an * T * 2);
-    uint32_t *gt = gate_all + g * T;
-    for (int s = threadIdx.x; s < T; s += 32 * PPC) {
-      const int2 v = __ldg(&lr2[s]);
-      gt[s] = (uint32_t)v.x | ((uint32_t)v.y << 16);
+  {
+    const int an = gate_ann[0];
+    if (an >= 0) {
+      const int2 *lr2 = reinterpret_cast<const int2 *>(a.lr + (size_t)an * T * 2);
+      for (int s = threadIdx.x; s < T; s += 32 * PPC) {
+        const int2 v = __ldg(&lr2[s]);
+        gate_all[s] = (uint32_t)v.x | ((uint32_t)v.y << 16);
+      }
     }
   }
   __syncthreads();
-  // this pixel's gate: staged copy 0 or 1, or (a third annulus in one group)
-  // global memory
-  const int gsel = gate_ann[0] == ann ? 0 : (gate_ann[1] == ann ? 1 : -1);
-  const int goff = gsel > 0 ? T : 0;
+  // this pixel's gate: the staged copy, or global memory (a second annulus
+  // in one group: groups that straddle an annulus edge)
+  const int gsel = gate_ann[0] == ann ? 0 : -1;
+  const int goff = 0;
   const int2 *gate_g = reinterpret_cast<const int2 *>(a.lr + (size_t)(ann < 0 ? 0 : ann) * T * 2);
 
   const int C = (T + 31) / 32;
