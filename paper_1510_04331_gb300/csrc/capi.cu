@@ -50,6 +50,10 @@ struct graphic_ctx {
   size_t img_bytes = 0;
   char *d_bscratch = nullptr;       // median PSF band path: per-pixel band tables
   size_t bscratch_bytes = 0;
+  char *d_lparam = nullptr;         // line-pass parameter tables
+  size_t lparam_bytes = 0;
+  cudaStream_t s_general = nullptr; // median PSF general path, overlapping the band path
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool prof = false;
   double prof_ms[GRAPHIC_K_COUNT] = {};
   int64_t prof_n[GRAPHIC_K_COUNT] = {};
@@ -153,7 +157,11 @@ int ensure(void **ptr, size_t *have, size_t need, bool pinned) {
 }
 
 // --- profiling ------------------------------------------------------------
-void prof_begin(graphic_ctx *c, int k) {
+void prof_begin(graphic_ctx *c, int k, cudaStream_t st);
+void prof_end(graphic_ctx *c, cudaStream_t st);
+void prof_begin(graphic_ctx *c, int k) { prof_begin(c, k, c->stream); }
+void prof_end(graphic_ctx *c) { prof_end(c, c->stream); }
+void prof_begin(graphic_ctx *c, int k, cudaStream_t st) {
   if (!c->prof) return;
   if (c->ev.size() < 2 * (c->ev_used + 1)) {
     cudaEvent_t a, b;
@@ -164,11 +172,11 @@ void prof_begin(graphic_ctx *c, int k) {
     c->ev_kernel.push_back(k);
   }
   c->ev_kernel[c->ev_used] = k;
-  cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+  cudaEventRecord(c->ev[2 * c->ev_used], st);
 }
-void prof_end(graphic_ctx *c) {
+void prof_end(graphic_ctx *c, cudaStream_t st) {
   if (!c->prof) return;
-  cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
+  cudaEventRecord(c->ev[2 * c->ev_used + 1], st);
   c->ev_used++;
 }
 void prof_collect(graphic_ctx *c) {
@@ -270,6 +278,19 @@ int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_
   if (!in_fs) in_fs = NN;
   if (!out_fs) out_fs = NN;
   const long long ch = chunk_frames(c, T, (size_t)NN * sizeof(float));
+  // per-frame shift parameters of both passes, once for all frames
+  const size_t pb = line_params_bytes(SHIFT_X, n, T);
+  int rc = ensure((void **)&c->d_lparam, &c->lparam_bytes, 2 * pb, false);
+  if (rc) return rc;
+  {
+    LineArgs a{};
+    a.p0 = p_dx;
+    a.p1 = p_dy;
+    a.n = n;
+    cudaError_t e = launch_line_params(SHIFT_X, a, T, c->d_lparam, c->stream);
+    if (e == cudaSuccess) e = launch_line_params(SHIFT_Y, a, T, c->d_lparam + pb, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "shift parameters");
+  }
   for (long long f0 = 0; f0 < T; f0 += ch) {
     const long long nf = std::min<long long>(ch, T - f0);
     LineArgs a{};
@@ -281,12 +302,15 @@ int enqueue_shift(graphic_ctx *c, const float *in, float *out, int64_t T, int32_
     a.in_fstride = in_fs;
     a.out_fstride = out_fs;
     a.n = n;
+    a.lp_lines = 1;
+    a.lp_tab = c->d_lparam + (size_t)f0 * (pb / T);
     prof_begin(c, GRAPHIC_K_SHIFT_X);
     cudaError_t e = line_pass(c, SHIFT_X, a, nf, c->stream);
     prof_end(c);
     if (e != cudaSuccess) return cuda_fail(e, "shift x pass");
     a.in = out + f0 * out_fs;
     a.in_fstride = out_fs;
+    a.lp_tab = c->d_lparam + pb + (size_t)f0 * (pb / T);
     prof_begin(c, GRAPHIC_K_SHIFT_Y);
     e = line_pass(c, SHIFT_Y, a, nf, c->stream);
     prof_end(c);
@@ -332,6 +356,9 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
   const long long ch = chunk_frames(c, T, (size_t)NM * sizeof(float));
   int rc = ensure((void **)&c->d_scratch, &c->scratch_bytes, (size_t)ch * NM * sizeof(float), false);
   if (rc) return rc;
+  // per-line shear parameters of a chunk: passes 1 and 3 share theirs
+  const size_t pb13 = line_params_bytes(ROT_P1, n, ch), pb2 = line_params_bytes(ROT_P2, n, ch);
+  if ((rc = ensure((void **)&c->d_lparam, &c->lparam_bytes, pb13 + pb2, false))) return rc;
   for (long long f0 = 0; f0 < T; f0 += ch) {
     const long long nf = std::min<long long>(ch, T - f0);
     LineArgs a{};
@@ -340,6 +367,13 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.q = p_q + f0;
     a.status = c->d_status;
     a.n = n;
+    {
+      cudaError_t e = launch_line_params(ROT_P1, a, nf, c->d_lparam, c->stream);
+      if (e == cudaSuccess) e = launch_line_params(ROT_P2, a, nf, c->d_lparam + pb13, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "shear parameters");
+    }
+    a.lp_tab = c->d_lparam;
+    a.lp_lines = line_params_lines(ROT_P1, n);
     // pass 1: frame rows (after rot90^q) -> scratch rows of 2n
     a.in = in + f0 * in_fs;
     a.out = c->d_scratch;
@@ -354,6 +388,8 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     a.out = c->d_scratch;
     a.in_fstride = NM;
     a.out_fstride = NM;
+    a.lp_tab = c->d_lparam + pb13;
+    a.lp_lines = line_params_lines(ROT_P2, n);
     prof_begin(c, GRAPHIC_K_ROT_P2);
     e = line_pass(c, ROT_P2, a, nf, c->stream);
     prof_end(c);
@@ -361,6 +397,8 @@ int enqueue_rotate(graphic_ctx *c, const float *in, float *out, int64_t T, int32
     // pass 3: scratch rows -> frame rows
     a.out = out + f0 * out_fs;
     a.out_fstride = out_fs;
+    a.lp_tab = c->d_lparam;
+    a.lp_lines = line_params_lines(ROT_P3, n);
     prof_begin(c, GRAPHIC_K_ROT_P3);
     e = line_pass(c, ROT_P3, a, nf, c->stream);
     prof_end(c);
@@ -580,9 +618,20 @@ int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int3
   a.mark = [](void *u, int kind, int begin) {
     graphic_ctx *cc = static_cast<graphic_ctx *>(u);
     const int id = kind == 0 ? GRAPHIC_K_ADI_MEDIAN : kind == 1 ? GRAPHIC_K_ADI_BAND_PREP : GRAPHIC_K_ADI_BAND_SWEEP;
-    if (begin) prof_begin(cc, id);
-    else prof_end(cc);
+    cudaStream_t st = (kind == 0 && cc->s_general) ? cc->s_general : cc->stream;
+    if (begin) prof_begin(cc, id, st);
+    else prof_end(cc, st);
   };
+  // the general path on its own stream, overlapping the band path
+  if (!c->s_general) {
+    if (cudaStreamCreateWithFlags(&c->s_general, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(GRAPHIC_ERR_CUDA, "stream for the median PSF general path");
+  }
+  a.st_general = c->s_general;
+  a.ev_fork = c->ev_fork;
+  a.ev_join = c->ev_join;
   int launched = 0;
   cudaError_t e = launch_adi_median(a, c->stream, &launched);
   if (e != cudaSuccess) return cuda_fail(e, "median PSF kernel");
@@ -1285,6 +1334,9 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_bscratch);
   c->d_bscratch = nullptr;
   c->bscratch_bytes = 0;
+  cudaFree(c->d_lparam);
+  c->d_lparam = nullptr;
+  c->lparam_bytes = 0;
   cudaFree(c->d_counters);
   cudaFree(c->d_gscratch);
   c->d_gscratch = nullptr;
@@ -1319,6 +1371,9 @@ int graphic_destroy(graphic_ctx *c) {
   for (cudaEvent_t e : c->gevents) cudaEventDestroy(e);
   if (c->ev_copy) cudaEventDestroy(c->ev_copy);
   if (c->s_copy) cudaStreamDestroy(c->s_copy);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->s_general) cudaStreamDestroy(c->s_general);
   for (cudaStream_t st : c->gstreams) cudaStreamDestroy(st);
   delete c;
   return GRAPHIC_OK;
@@ -2026,7 +2081,7 @@ const char *graphic_kernel_name(int32_t k) {
 int graphic_workspace_bytes(graphic_ctx *c, int64_t *bytes) {
   if (!c || !bytes) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
   *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->gscratch_bytes + c->cube_bytes + c->img_bytes +
-                     c->counters_bytes + c->bscratch_bytes);
+                     c->counters_bytes + c->bscratch_bytes + c->lparam_bytes);
   return GRAPHIC_OK;
 }
 

@@ -283,7 +283,10 @@ __device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, i
   }
   if (tid < 2 * LPC && (!SAME_D || tid == 0)) {
     const int gl = 2 * cx * LPC + tid;
-    make_param(lp[tid], line_shift<KIND>(a, f, gl, N), M);
+    if (a.lp_tab)
+      lp[tid] = reinterpret_cast<const LineParam *>(a.lp_tab)[f * a.lp_lines + (SAME_D ? 0 : gl)];
+    else
+      make_param(lp[tid], line_shift<KIND>(a, f, gl, N), M);
   }
   __syncthreads();
 
@@ -563,7 +566,12 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
     else id = (a.p0[f] == 0.0 && a.p1[f] == 0.0);
     ident_s = id ? 1 : 0;
   }
-  if (lane < 2 && (!SAME_D || lane == 0)) make_param(lp[p][lane], line_shift<KIND>(a, f, line0 + lane, N), M);
+  if (lane < 2 && (!SAME_D || lane == 0)) {
+    if (a.lp_tab)
+      lp[p][lane] = reinterpret_cast<const LineParam *>(a.lp_tab)[f * a.lp_lines + (SAME_D ? 0 : line0 + lane)];
+    else
+      make_param(lp[p][lane], line_shift<KIND>(a, f, line0 + lane, N), M);
+  }
   __syncthreads();
 
   bool bad = false;
@@ -762,6 +770,7 @@ cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
     b.q = a.q ? a.q + f0 : nullptr;
     b.in_tab = a.in_tab ? a.in_tab + f0 : nullptr;
     b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
+    b.lp_tab = a.lp_tab ? reinterpret_cast<const LineParam *>(a.lp_tab) + f0 * a.lp_lines : nullptr;
     dim3 grid(NLINES / (2 * PPC), (unsigned)nf);
     line_pass_w32<KIND><<<grid, 32 * PPC, 0, st>>>(b);
     cudaError_t e = cudaGetLastError();
@@ -906,6 +915,7 @@ cudaError_t launch_one(const LineArgs &a, long long n_frames, cudaStream_t st) {
     b.q = a.q ? a.q + f0 : nullptr;
     b.in_tab = a.in_tab ? a.in_tab + f0 : nullptr;
     b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
+    b.lp_tab = a.lp_tab ? reinterpret_cast<const LineParam *>(a.lp_tab) + f0 * a.lp_lines : nullptr;
     dim3 grid(NLINES / (2 * LPC), (unsigned)nf);
     line_pass_kernel<M, KIND><<<grid, 256, smem, st>>>(b);
     cudaError_t e = cudaGetLastError();
@@ -940,6 +950,42 @@ bool configure_m() {
 }
 
 }  // namespace
+
+// One thread per line: the line's shift parameters in FP64 (the arithmetic
+// each CTA of the passes would otherwise do on GB300's narrow FP64 pipe).
+template <int KIND>
+__global__ void __launch_bounds__(256) line_param_kernel(const LineArgs a, long long n_frames, int lines,
+                                                        LineParam *out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_frames * lines) return;
+  const long long f = idx / lines;
+  const int line = (int)(idx - f * lines);
+  make_param(out[idx], line_shift<KIND>(a, f, line, a.n), 2 * a.n);
+}
+
+int line_params_lines(LineKind kind, int n) {
+  return (kind == SHIFT_X || kind == SHIFT_Y) ? 1 : (kind == ROT_P2 ? 2 * n : n);
+}
+
+size_t line_params_bytes(LineKind kind, int n, long long n_frames) {
+  return (size_t)n_frames * line_params_lines(kind, n) * sizeof(LineParam);
+}
+
+cudaError_t launch_line_params(LineKind kind, const LineArgs &a, long long n_frames, void *out, cudaStream_t st) {
+  const int lines = line_params_lines(kind, a.n);
+  const long long total = n_frames * lines;
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  LineParam *o = reinterpret_cast<LineParam *>(out);
+  switch (kind) {
+    case SHIFT_X: line_param_kernel<SHIFT_X><<<grid, 256, 0, st>>>(a, n_frames, lines, o); break;
+    case SHIFT_Y: line_param_kernel<SHIFT_Y><<<grid, 256, 0, st>>>(a, n_frames, lines, o); break;
+    case ROT_P1:
+    case ROT_P3: line_param_kernel<ROT_P1><<<grid, 256, 0, st>>>(a, n_frames, lines, o); break;
+    case ROT_P2: line_param_kernel<ROT_P2><<<grid, 256, 0, st>>>(a, n_frames, lines, o); break;
+  }
+  return cudaGetLastError();
+}
 
 int geom_init_device() {
   if (!(configure_m<128>() && configure_m<256>() && configure_m<512>() && configure_m<1024>() &&

@@ -31,6 +31,12 @@ struct LineArgs {
   int n;                 // frame side
   const float *const *in_tab;  // optional: frame f reads in_tab[f] instead of in + f in_fstride
   float *const *out_tab;       // optional: frame f writes out_tab[f] instead of out + f out_fstride
+  // optional: the per-line shift parameters (phase splits, Nyquist weight,
+  // phasor steps) precomputed by launch_line_params, lp_lines per frame
+  // (1 for the shift passes, whose lines of a frame share their shift);
+  // null: each CTA computes its lines' parameters itself (FP64)
+  const void *lp_tab;
+  int lp_lines;
 };
 
 // Record `msg` as the calling thread's last error (graphic_last_error) and
@@ -98,6 +104,13 @@ int geom_init_device();   // uploads the twiddle tables of the current device (0
 // variant_1024: 1024-point lines by one warp per line pair (1) or the generic kernel (0)
 cudaError_t launch_line_pass(LineKind kind, const LineArgs &a, long long n_frames, cudaStream_t st,
                              int variant_1024 = 1);
+// Parameter tables for the line passes (geom.cu): the parameters of every
+// line of n_frames frames of pass `kind` (ROT_P1 and ROT_P3 share theirs),
+// computed in FP64 by one thread per line into `out`, line_params_bytes(kind,
+// n, n_frames) bytes; the lines per frame of the table is line_params_lines.
+int line_params_lines(LineKind kind, int n);
+size_t line_params_bytes(LineKind kind, int n, long long n_frames);
+cudaError_t launch_line_params(LineKind kind, const LineArgs &a, long long n_frames, void *out, cudaStream_t st);
 
 // Uneven batches (one persistent launch): per-frame descriptor ...
 struct BatchFrame {
@@ -174,6 +187,11 @@ struct AdiArgs {
   // 1 = band preparation (and the zero groups), 2 = band sweep
   void (*mark)(void *user, int kind, int begin);
   void *mark_user;
+  // optional: a second stream for the general path, which works on pixels
+  // disjoint from the band path's (fork after ev_fork is recorded on the
+  // main stream, join through ev_join); null: everything on the main stream
+  cudaStream_t st_general;
+  cudaEvent_t ev_fork, ev_join;
 };
 // *launched (may be null) receives the number of kernels launched (1 to 3:
 // general path, band path W <= 16, band path W = 32).

@@ -399,7 +399,12 @@ __global__ void __launch_bounds__(128, TC_MIN_CTAS) line_pass_tc(const LineArgs 
     const int pair = blockIdx.x * TC_PPC + pp;
     if (pair >= pairs) break;
     const int line0 = 2 * pair;
-    if (tid < 2 && (!SAME_D || tid == 0)) make_param(lp[tid], line_shift<KIND>(a, f, line0 + tid, N), M);
+    if (tid < 2 && (!SAME_D || tid == 0)) {
+      if (a.lp_tab)
+        lp[tid] = reinterpret_cast<const LineParam *>(a.lp_tab)[f * a.lp_lines + (SAME_D ? 0 : line0 + tid)];
+      else
+        make_param(lp[tid], line_shift<KIND>(a, f, line0 + tid, N), M);
+    }
     __syncthreads();
 
     bool bad = false;
@@ -577,6 +582,7 @@ cudaError_t launch_kind(const LineArgs &a, long long n_frames, cudaStream_t st) 
     b.q = a.q ? a.q + f0 : nullptr;
     b.in_tab = a.in_tab ? a.in_tab + f0 : nullptr;
     b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
+    b.lp_tab = a.lp_tab ? reinterpret_cast<const LineParam *>(a.lp_tab) + f0 * a.lp_lines : nullptr;
     dim3 grid((NLINES / 2 + TC_PPC - 1) / TC_PPC, (unsigned)nf);
     line_pass_tc<KIND, F16><<<grid, 128, SM_BYTES + 1024, st>>>(b);
     cudaError_t e = cudaGetLastError();
