@@ -52,8 +52,8 @@ struct graphic_ctx {
   size_t bscratch_bytes = 0;
   char *d_lparam = nullptr;         // line-pass parameter tables
   size_t lparam_bytes = 0;
-  cudaStream_t s_general = nullptr; // median PSF general path, overlapping the band path
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  char *d_gparam = nullptr;         // grouped executor: parameter tables, one region per branch
+  size_t gparam_bytes = 0;
   bool prof = false;
   double prof_ms[GRAPHIC_K_COUNT] = {};
   int64_t prof_n[GRAPHIC_K_COUNT] = {};
@@ -157,11 +157,7 @@ int ensure(void **ptr, size_t *have, size_t need, bool pinned) {
 }
 
 // --- profiling ------------------------------------------------------------
-void prof_begin(graphic_ctx *c, int k, cudaStream_t st);
-void prof_end(graphic_ctx *c, cudaStream_t st);
-void prof_begin(graphic_ctx *c, int k) { prof_begin(c, k, c->stream); }
-void prof_end(graphic_ctx *c) { prof_end(c, c->stream); }
-void prof_begin(graphic_ctx *c, int k, cudaStream_t st) {
+void prof_begin(graphic_ctx *c, int k) {
   if (!c->prof) return;
   if (c->ev.size() < 2 * (c->ev_used + 1)) {
     cudaEvent_t a, b;
@@ -172,11 +168,11 @@ void prof_begin(graphic_ctx *c, int k, cudaStream_t st) {
     c->ev_kernel.push_back(k);
   }
   c->ev_kernel[c->ev_used] = k;
-  cudaEventRecord(c->ev[2 * c->ev_used], st);
+  cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
 }
-void prof_end(graphic_ctx *c, cudaStream_t st) {
+void prof_end(graphic_ctx *c) {
   if (!c->prof) return;
-  cudaEventRecord(c->ev[2 * c->ev_used + 1], st);
+  cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
   c->ev_used++;
 }
 void prof_collect(graphic_ctx *c) {
@@ -618,20 +614,9 @@ int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int3
   a.mark = [](void *u, int kind, int begin) {
     graphic_ctx *cc = static_cast<graphic_ctx *>(u);
     const int id = kind == 0 ? GRAPHIC_K_ADI_MEDIAN : kind == 1 ? GRAPHIC_K_ADI_BAND_PREP : GRAPHIC_K_ADI_BAND_SWEEP;
-    cudaStream_t st = (kind == 0 && cc->s_general) ? cc->s_general : cc->stream;
-    if (begin) prof_begin(cc, id, st);
-    else prof_end(cc, st);
+    if (begin) prof_begin(cc, id);
+    else prof_end(cc);
   };
-  // the general path on its own stream, overlapping the band path
-  if (!c->s_general) {
-    if (cudaStreamCreateWithFlags(&c->s_general, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
-      return fail(GRAPHIC_ERR_CUDA, "stream for the median PSF general path");
-  }
-  a.st_general = c->s_general;
-  a.ev_fork = c->ev_fork;
-  a.ev_join = c->ev_join;
   int launched = 0;
   cudaError_t e = launch_adi_median(a, c->stream, &launched);
   if (e != cudaSuccess) return cuda_fail(e, "median PSF kernel");
@@ -1028,6 +1013,19 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
   const int R = std::max(1, std::min<int>(c->group_streams, (int)waves.size()));
   int rc;
   if (slot_bytes && (rc = ensure((void **)&c->d_gscratch, &c->gscratch_bytes, slot_bytes * R, false))) return rc;
+  // per-line shift parameter tables of a wave (one region per branch):
+  // shift x and y per frame, then shears of rotation passes 1/3 and 2
+  auto wave_tab_bytes = [](const GroupWave &w) -> size_t {
+    size_t b = 0;
+    if (w.mask & GRAPHIC_PASS_SHIFT) b += 2 * line_params_bytes(SHIFT_X, w.n, w.nf);
+    if (w.mask & GRAPHIC_PASS_ROTATE)
+      b += line_params_bytes(ROT_P1, w.n, w.nf) + line_params_bytes(ROT_P2, w.n, w.nf);
+    return b;
+  };
+  size_t tab_bytes = 16;
+  for (const GroupWave &w : waves) tab_bytes = std::max(tab_bytes, wave_tab_bytes(w));
+  tab_bytes = (tab_bytes + 255) & ~(size_t)255;
+  if ((rc = ensure((void **)&c->d_gparam, &c->gparam_bytes, tab_bytes * R, false))) return rc;
   // plan: per frame tables in the sorted order
   std::vector<const float *> tin(nframes), trin(nframes);
   std::vector<float *> tout(nframes);
@@ -1059,7 +1057,8 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
   std::vector<long long> key = {(long long)(uintptr_t)c->h_plan, (long long)(uintptr_t)c->d_plan,
                                 (long long)pb.buf.size(), (long long)(uintptr_t)c->d_gscratch, (long long)slot_bytes,
                                 (long long)(uintptr_t)c->d_status, R, c->variant_1024, c->precision,
-                                (long long)(uintptr_t)c->stream};
+                                (long long)(uintptr_t)c->stream, (long long)(uintptr_t)c->d_gparam,
+                                (long long)tab_bytes};
   for (const GroupWave &w : waves) {
     key.push_back(w.n);
     key.push_back(w.mask);
@@ -1083,6 +1082,7 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
       const int r = (int)(wi % R);
       cudaStream_t st = r ? c->gstreams[r] : s0;
       const long long NM = 2ll * w.n * w.n;
+      char *tab = c->d_gparam + (size_t)r * tab_bytes;
       LineArgs a{};
       a.status = c->d_status;
       a.n = w.n;
@@ -1091,9 +1091,16 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
         a.out_tab = at<float *>(c, o_out) + w.f0;
         a.p0 = at<double>(c, o_dx) + w.f0;
         a.p1 = at<double>(c, o_dy) + w.f0;
-        e = line_pass(c, SHIFT_X, a, w.nf, st);
+        const size_t pb1 = line_params_bytes(SHIFT_X, w.n, w.nf);
+        e = launch_line_params(SHIFT_X, a, w.nf, tab, st);
+        if (e == cudaSuccess) e = launch_line_params(SHIFT_Y, a, w.nf, tab + pb1, st);
+        a.lp_lines = 1;
+        a.lp_tab = tab;
+        if (e == cudaSuccess) e = line_pass(c, SHIFT_X, a, w.nf, st);
         a.in_tab = at<const float *>(c, o_out) + w.f0;
+        a.lp_tab = tab + pb1;
         if (e == cudaSuccess) e = line_pass(c, SHIFT_Y, a, w.nf, st);
+        tab += 2 * pb1;
       }
       if ((w.mask & GRAPHIC_PASS_ROTATE) && e == cudaSuccess) {
         float *slot = c->d_gscratch + (size_t)r * (slot_bytes / sizeof(float));
@@ -1106,13 +1113,22 @@ int batch_grouped(graphic_ctx *c, const graphic_batch_item *items, int32_t n_ite
         b.in_tab = at<const float *>(c, o_rin) + w.f0;
         b.out = slot;
         b.out_fstride = NM;
-        e = line_pass(c, ROT_P1, b, w.nf, st);
+        const size_t pb13 = line_params_bytes(ROT_P1, w.n, w.nf);
+        e = launch_line_params(ROT_P1, b, w.nf, tab, st);
+        if (e == cudaSuccess) e = launch_line_params(ROT_P2, b, w.nf, tab + pb13, st);
+        b.lp_tab = tab;
+        b.lp_lines = line_params_lines(ROT_P1, w.n);
+        if (e == cudaSuccess) e = line_pass(c, ROT_P1, b, w.nf, st);
         b.in_tab = nullptr;
         b.in = slot;
         b.in_fstride = NM;
+        b.lp_tab = tab + pb13;
+        b.lp_lines = line_params_lines(ROT_P2, w.n);
         if (e == cudaSuccess) e = line_pass(c, ROT_P2, b, w.nf, st);
         b.out = nullptr;
         b.out_tab = at<float *>(c, o_out) + w.f0;
+        b.lp_tab = tab;
+        b.lp_lines = line_params_lines(ROT_P3, w.n);
         if (e == cudaSuccess) e = line_pass(c, ROT_P3, b, w.nf, st);
       }
     }
@@ -1280,7 +1296,10 @@ size_t graphic::ctx_workspace_bound(const graphic_ctx *c, int32_t mode) {
   if (mode == GRAPHIC_BATCH_AUTO) mode = c->batch_mode;
   const size_t mb = 1ull << 20;
   size_t ws = 64 * mb;   // plans, tables, counters
-  if (mode == GRAPHIC_BATCH_GROUPED) ws += (size_t)c->group_streams * std::max<size_t>(c->group_budget_mb * mb, 8 * mb);
+  // grouped: the branches' rotation scratch and their parameter tables (at
+  // most half the scratch: 3n lines of 80 bytes per frame against 8 n^2)
+  if (mode == GRAPHIC_BATCH_GROUPED)
+    ws += (size_t)c->group_streams * std::max<size_t>(c->group_budget_mb * mb, 8 * mb) * 3 / 2;
   else if (mode == GRAPHIC_BATCH_PERSISTENT) ws += 2 * std::max<size_t>(c->batch_budget_mb * mb, 8 * mb);
   else ws += std::max<size_t>((size_t)c->chunk_mb * mb * 2, 8 * mb);
   return ws;
@@ -1337,6 +1356,9 @@ int graphic_release(graphic_ctx *c) {
   cudaFree(c->d_lparam);
   c->d_lparam = nullptr;
   c->lparam_bytes = 0;
+  cudaFree(c->d_gparam);
+  c->d_gparam = nullptr;
+  c->gparam_bytes = 0;
   cudaFree(c->d_counters);
   cudaFree(c->d_gscratch);
   c->d_gscratch = nullptr;
@@ -1371,9 +1393,6 @@ int graphic_destroy(graphic_ctx *c) {
   for (cudaEvent_t e : c->gevents) cudaEventDestroy(e);
   if (c->ev_copy) cudaEventDestroy(c->ev_copy);
   if (c->s_copy) cudaStreamDestroy(c->s_copy);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->s_general) cudaStreamDestroy(c->s_general);
   for (cudaStream_t st : c->gstreams) cudaStreamDestroy(st);
   delete c;
   return GRAPHIC_OK;
@@ -2081,7 +2100,7 @@ const char *graphic_kernel_name(int32_t k) {
 int graphic_workspace_bytes(graphic_ctx *c, int64_t *bytes) {
   if (!c || !bytes) return fail(GRAPHIC_ERR_INVALID_ARG, "bad arguments");
   *bytes = (int64_t)(c->d_plan_bytes + c->scratch_bytes + c->gscratch_bytes + c->cube_bytes + c->img_bytes +
-                     c->counters_bytes + c->bscratch_bytes + c->lparam_bytes);
+                     c->counters_bytes + c->bscratch_bytes + c->lparam_bytes + c->gparam_bytes);
   return GRAPHIC_OK;
 }
 

@@ -538,15 +538,22 @@ __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *
   __syncwarp();
 }
 
-// Register budget for 4 resident CTAs per SM (measured faster than 3 for
-// every kind once the column passes move whole sectors; small spills).
+// Line pairs (warps) per CTA: 4 (column passes move 32-byte row pieces of
+// their 8 adjacent columns; 8 pairs per CTA with 64-byte pieces measured
+// slower: shift columns 2.46 -> 2.70 ms per survey step).  Register budget
+// for 16 resident warps per SM (measured faster than 12 for every kind).
 template <int KIND>
-__global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
-  constexpr int M = 1024, N = 512, PPC = 4;
+constexpr int w32_ppc() { return 4; }
+constexpr size_t w32_smem_bytes(int ppc) { return (size_t)ppc * (1024 + 1024 / 32) * sizeof(float2); }
+
+template <int KIND>
+__global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) line_pass_w32(const LineArgs a) {
+  constexpr int M = 1024, N = 512, PPC = w32_ppc<KIND>();
   constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
   constexpr int NIN = (KIND == ROT_P3) ? M : N;
   constexpr int NOUT = (KIND == ROT_P1) ? M : N;
-  __shared__ float2 sbuf[PPC][M + M / 32];
+  extern __shared__ float2 w32_smem[];
+  float2 (*sbuf)[M + M / 32] = reinterpret_cast<float2 (*)[M + M / 32]>(w32_smem);   // [PPC][M + M/32]
   __shared__ LineParam lp[PPC][2];
   __shared__ int ident_s;
 
@@ -603,14 +610,15 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
   }
 
   // ---- load: v[m] = element lane + 32 m of the line pair -----------------
-  // Column passes: the CTA's 8 adjacent columns are read row by row as
+  // Column passes: the CTA's 2 PPC adjacent columns are read row by row as
   // 16-byte pieces (whole sectors) into the per-pair buffers first.
   constexpr bool COLS = (KIND == SHIFT_Y || KIND == ROT_P2);
   constexpr int RS = (KIND == ROT_P2) ? M : N;     // row stride of a column pass
+  constexpr int HP = PPC / 2;                      // 16-byte pieces per row of the CTA's columns
   const int col0 = 2 * PPC * blockIdx.x;           // first column of the CTA
   if constexpr (COLS) {
-    for (int i = threadIdx.x; i < 2 * NIN; i += 32 * PPC) {
-      const int row = i >> 1, h = i & 1;
+    for (int i = threadIdx.x; i < HP * NIN; i += 32 * PPC) {
+      const int row = i / HP, h = i % HP;
       const float4 q4 = *reinterpret_cast<const float4 *>(fin + (size_t)row * RS + col0 + 4 * h);
       sbuf[2 * h][pad32(row)] = make_float2(q4.x, q4.y);
       sbuf[2 * h + 1][pad32(row)] = make_float2(q4.z, q4.w);
@@ -731,8 +739,8 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
     for (int r = 0; r < 32; r++)
       if (32 * r < NOUT) buf[pad32(lane + 32 * r)] = make_float2(v[r].x, -v[r].y);
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * NOUT; i += 32 * PPC) {
-      const int row = i >> 1, h = i & 1;
+    for (int i = threadIdx.x; i < HP * NOUT; i += 32 * PPC) {
+      const int row = i / HP, h = i % HP;
       const float2 e0 = sbuf[2 * h][pad32(row)], e1 = sbuf[2 * h + 1][pad32(row)];
       *reinterpret_cast<float4 *>(fout + (size_t)row * RS + col0 + 4 * h) = make_float4(e0.x, e0.y, e1.x, e1.y);
     }
@@ -758,7 +766,7 @@ __global__ void __launch_bounds__(128, 4) line_pass_w32(const LineArgs a) {
 
 template <int KIND>
 cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
-  constexpr int M = 1024, N = 512, PPC = 4;
+  constexpr int M = 1024, N = 512, PPC = w32_ppc<KIND>();
   constexpr int NLINES = (KIND == ROT_P2) ? M : N;
   for (long long f0 = 0; f0 < n_frames; f0 += 65535) {
     const long long nf = (n_frames - f0 < 65535) ? (n_frames - f0) : 65535;
@@ -772,7 +780,7 @@ cudaError_t launch_w32(const LineArgs &a, long long n_frames, cudaStream_t st) {
     b.out_tab = a.out_tab ? a.out_tab + f0 : nullptr;
     b.lp_tab = a.lp_tab ? reinterpret_cast<const LineParam *>(a.lp_tab) + f0 * a.lp_lines : nullptr;
     dim3 grid(NLINES / (2 * PPC), (unsigned)nf);
-    line_pass_w32<KIND><<<grid, 32 * PPC, 0, st>>>(b);
+    line_pass_w32<KIND><<<grid, 32 * PPC, w32_smem_bytes(PPC), st>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -991,6 +999,15 @@ int geom_init_device() {
   if (!(configure_m<128>() && configure_m<256>() && configure_m<512>() && configure_m<1024>() &&
         configure_m<2048>()))
     return -1;
+  {
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(line_pass_w32<SHIFT_X>, at, (int)w32_smem_bytes(w32_ppc<SHIFT_X>())) != cudaSuccess ||
+        cudaFuncSetAttribute(line_pass_w32<SHIFT_Y>, at, (int)w32_smem_bytes(w32_ppc<SHIFT_Y>())) != cudaSuccess ||
+        cudaFuncSetAttribute(line_pass_w32<ROT_P1>, at, (int)w32_smem_bytes(w32_ppc<ROT_P1>())) != cudaSuccess ||
+        cudaFuncSetAttribute(line_pass_w32<ROT_P2>, at, (int)w32_smem_bytes(w32_ppc<ROT_P2>())) != cudaSuccess ||
+        cudaFuncSetAttribute(line_pass_w32<ROT_P3>, at, (int)w32_smem_bytes(w32_ppc<ROT_P3>())) != cudaSuccess)
+      return -1;
+  }
   // the persistent batch kernel is launched inside stream capture: set its
   // shared-memory limit here, per device, outside any capture
   if (cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -187,11 +187,6 @@ struct AdiArgs {
   // 1 = band preparation (and the zero groups), 2 = band sweep
   void (*mark)(void *user, int kind, int begin);
   void *mark_user;
-  // optional: a second stream for the general path, which works on pixels
-  // disjoint from the band path's (fork after ev_fork is recorded on the
-  // main stream, join through ev_join); null: everything on the main stream
-  cudaStream_t st_general;
-  cudaEvent_t ev_fork, ev_join;
 };
 // *launched (may be null) receives the number of kernels launched (1 to 3:
 // general path, band path W <= 16, band path W = 32).

@@ -703,30 +703,11 @@ cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched) 
   // general kernel first: it reads every pixel of its 8-pixel groups and
   // writes only the 4-pixel halves that are not on the band path; the band
   // path's groups (psf_band.cu) are disjoint from those halves
-  // with a second stream the general path overlaps the band path (its CTAs
-  // are few and long: one per 8 pixels of the innermost annuli)
-  const bool fork = a.st_general && a.ev_fork && a.ev_join && a.wmax > 0;
-  cudaStream_t sg = fork ? a.st_general : st;
-  cudaError_t e = cudaSuccess;
-  if (fork) {
-    // the band path is enqueued first, so that the general path's few long
-    // CTAs take the SMs its launches leave free (the tail of its last wave)
-    // rather than holding shared memory the band kernels need
-    e = cudaEventRecord(a.ev_fork, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(sg, a.ev_fork, 0);
-    if (e == cudaSuccess) e = launch_adi_band(a, st, &nl);
-    if (e != cudaSuccess) return e;
-  }
   if (a.mark) a.mark(a.mark_user, 0, 1);
-  e = launch_adi_general(a, sg, tcap);
+  cudaError_t e = launch_adi_general(a, st, tcap);
   if (a.mark) a.mark(a.mark_user, 0, 0);
   nl += (e == cudaSuccess);
   if (e != cudaSuccess || a.wmax == 0) return e;
-  if (fork) {
-    e = cudaEventRecord(a.ev_join, sg);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, a.ev_join, 0);
-    return e;
-  }
   return launch_adi_band(a, st, &nl);
 }
 
