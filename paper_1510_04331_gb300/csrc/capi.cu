@@ -587,8 +587,10 @@ AdiOffsets add_adi_plan(PlanBuilder &pb, const AdiPlanHost &ap, int64_t T) {
 int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
                     const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann,
                     const int *p_ab, const uint32_t *p_evq, const int *p_groups, const std::vector<int> &class_off,
-                    char *band_scratch, size_t band_scratch_cap, long long in_fs, long long out_fs) {
+                    char *band_scratch, size_t band_scratch_cap, long long in_fs, long long out_fs,
+                    bool perm_id) {
   AdiArgs a{};
+  a.perm_id = perm_id ? 1 : 0;
   a.in_fs = in_fs ? in_fs : (long long)n * n;
   a.out_fs = out_fs ? out_fs : (long long)n * n;
   a.band_scratch_cap = band_scratch_cap;
@@ -646,6 +648,8 @@ const T *at(const graphic_ctx *c, size_t off) {
 
 int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const AdiPlanHost &ap,
                 const AdiOffsets &o, long long in_fs = 0, long long out_fs = 0) {
+  bool perm_id = true;
+  for (int64_t t = 0; t < T && perm_id; t++) perm_id = ap.perm[t] == (int)t;
   const size_t need = band_scratch_bytes(ap, T);
   if (need) {
     int rc = ensure((void **)&c->d_bscratch, &c->bscratch_bytes, need, false);
@@ -654,7 +658,7 @@ int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t 
   return enqueue_adi_raw(c, in, out, T, n, at<int>(c, o.perm), at<int>(c, o.lr), at<double>(c, o.e2),
                          at<int>(c, o.band), ap.wmax, (int)ap.edge2.size() - 1,
                          ap.ab.empty() ? nullptr : at<int>(c, o.ab), at<uint32_t>(c, o.evq), at<int>(c, o.groups),
-                         ap.class_off, c->d_bscratch, c->bscratch_bytes, in_fs, out_fs);
+                         ap.class_off, c->d_bscratch, c->bscratch_bytes, in_fs, out_fs, perm_id);
 }
 
 // Full reduction of the device cube `in` (work may equal in).  With host_in,

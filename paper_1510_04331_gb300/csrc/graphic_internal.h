@@ -163,6 +163,7 @@ struct AdiArgs {
   const float *in;
   float *out;
   const int *perm;       // [T] frame index at angle-sorted position s
+  int perm_id;           // 1: perm is the identity (frames already in angle order)
   const int *lr;         // [A][T][2] (L, R) of the reference set of sorted frame s in annulus a
   const int *ab;         // [T][2] time window (A, B) of sorted frame s, A <= L <= R <= B (null: [0, T));
                          // the reference set is [A, L) u [R, B)

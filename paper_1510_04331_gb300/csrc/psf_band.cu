@@ -190,8 +190,12 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
 
   if (lane == 0) ann_s[w] = annulus_of(p0 + w, a.n, a.edge2, a.n_ann);
   // the group's 4 pixels of every frame, angle order: one 16-byte copy each
-  for (int s = threadIdx.x; s < T; s += 32 * PPC)
-    cp_async16(keys + KS * s, a.in + (long long)__ldg(&a.perm[s]) * a.in_fs + p0);
+  if (a.perm_id) {
+    for (int s = threadIdx.x; s < T; s += 32 * PPC) cp_async16(keys + KS * s, a.in + (long long)s * a.in_fs + p0);
+  } else {
+    for (int s = threadIdx.x; s < T; s += 32 * PPC)
+      cp_async16(keys + KS * s, a.in + (long long)__ldg(&a.perm[s]) * a.in_fs + p0);
+  }
   cp_async_wait_all();
   __syncthreads();
   // from here on every warp works alone, on its own pixel's column
@@ -490,7 +494,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
     for (int q = threadIdx.x; q < SWK * 32; q += 32 * PPC) {
       const int kk = q >> 5, cc = q & 31;
       const int i = cc * C + b * SWK + kk;
-      if (b * SWK + kk < C && i < T) cp_async16(dst + q, a.in + (long long)__ldg(&a.perm[i]) * a.in_fs + p0);
+      if (b * SWK + kk < C && i < T)
+        cp_async16(dst + q, a.in + (long long)(a.perm_id ? i : __ldg(&a.perm[i])) * a.in_fs + p0);
     }
     cp_async_commit();
   };
@@ -610,19 +615,20 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
         if (t >= base && t < base + pc) {
           const int pos = nth_set(wd, t - base);
           float med = key2f(skeys[wi * 32 + pos]);
-          if ((nset & 1) == 0) {
-            // the next member: a higher bit of this word, else the first of a later word
-            uint32_t rest = pos < 31 ? (wd & (0xfffffffeu << pos)) : 0u;
-            int wn = wi;
-            while (rest == 0u && wn + 1 < WC) {
-              wn++;
-              rest = bm[wn * 32 + c];
-            }
-            if (rest) {
-              med = (med + key2f(skeys[wn * 32 + __ffs(rest) - 1])) * 0.5f;
-            } else {
-              fail = true;
-            }
+          // the next member, needed for an even |S_i| (found for every lane:
+          // the lanes' parities differ, so a branch would run both ways):
+          // a higher bit of this word, else the first of a later word
+          uint32_t rest = pos < 31 ? (wd & (0xfffffffeu << pos)) : 0u;
+          int wn = wi;
+          while (rest == 0u && wn + 1 < WC) {
+            wn++;
+            rest = bm[wn * 32 + c];
+          }
+          const bool even = (nset & 1) == 0;
+          const float hi = key2f(skeys[rest ? wn * 32 + __ffs(rest) - 1 : wi * 32 + pos]);
+          if (even) {
+            if (rest) med = (med + hi) * 0.5f;
+            else fail = true;
           }
           res = reinterpret_cast<const float *>(vb)[(kk * 32 + c) * 4 + w] - med;
         } else {
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
       const int i = cc * C + b * SWK + kk;
       if (b * SWK + kk < C && i < T) {
         const float4 r4 = reinterpret_cast<const float4 *>(obuf)[q];
-        *reinterpret_cast<float4 *>(a.out + (long long)__ldg(&a.perm[i]) * a.out_fs + p0) = r4;
+        *reinterpret_cast<float4 *>(a.out + (long long)(a.perm_id ? i : __ldg(&a.perm[i])) * a.out_fs + p0) = r4;
       }
     }
   }

@@ -7,20 +7,23 @@
 // iterations and requests finished on the device; they touch only atomics
 // and the condition variable.  The mutex is never held across a CUDA call.
 //
-// Streams.  s_in carries the copies in (plan, cube), s_out the copies out
-// (result, status), s_comp the kernels: a copy-out that waits for a collapse
-// never holds up a later request's copy-in.  A request joins an iteration's
-// shift stage once its copy-in has completed (so the kernels never wait on a
-// copy while other work is ready), and its copy-out waits on the event
-// recorded after its collapse.
+// Streams.  s_in carries the copies in (plan, cube) and each request's
+// shift, enqueued piece by piece right behind the piece's copy (so a request
+// is shifted while the rest of its cube is still landing, as in a lone
+// reduction of host buffers); s_out the copies out (result, status); s_comp
+// the other kernels: a copy-out that waits for a collapse never holds up a
+// later request's copy-in.  A request joins an iteration's median stage once
+// its copy-in and shift have completed (so the kernels never wait on a copy
+// while other work is ready), and its copy-out waits on the event recorded
+// after its collapse.
 //
 // Iterations.  Each issued iteration takes every resident request one stage
-// on: ADMITTED (copied in) -> shift, SHIFTED -> median PSF subtraction,
-// SUBTRACTED -> derotation, ROTATED -> collapse + copy-out.  Shift and
-// derotation items of one iteration form one uneven batch on one of two
-// library contexts (alternating, so that a context's host plan buffer is
-// not rewritten while the other iteration's copy of it may still be pending:
-// at most two iterations are in flight).
+// on: ADMITTED (copied in and shifted) -> median PSF subtraction,
+// SUBTRACTED -> derotation, ROTATED -> collapse + copy-out.  The derotation
+// items of one iteration form one uneven batch on one of two library
+// contexts (alternating, so that a context's host plan buffer is not
+// rewritten while the other iteration's copy of it may still be pending: at
+// most two iterations are in flight).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -113,6 +116,8 @@ struct Req {
   size_t cube_bytes = 0, out_bytes = 0, plan_bytes = 0, plan_dev_bytes = 0;
   size_t off_cube = Arena::kNone, off_out = Arena::kNone, off_plan = Arena::kNone;
   size_t o_perm = 0, o_lr = 0, o_e2 = 0, o_band = 0, o_evq = 0, o_groups = 0;   // within the plan
+  size_t o_dx = 0, o_dy = 0;   // staged shifts
+  size_t o_ptab = 0;           // device only (after the staged part): the shift passes' parameter tables
   // pinned staging: plan copy-in, result copy-out
   size_t stage_bytes = 0, off_stage = Arena::kNone;
   int slot = -1;   // per-request device status word
@@ -263,14 +268,43 @@ int start_copy_in(graphic_server *s, Req *r) {
   memcpy(hp + r->o_band, r->ap.band.data(), r->ap.band.size() * sizeof(int));
   memcpy(hp + r->o_evq, r->ap.evq.data(), r->ap.evq.size() * sizeof(uint32_t));
   memcpy(hp + r->o_groups, r->ap.groups.data(), r->ap.groups.size() * sizeof(int));
-  cudaError_t e = cudaMemcpyAsync(s->d_arena + r->off_plan, hp, r->plan_bytes, cudaMemcpyHostToDevice, s->s_in);
+  memcpy(hp + r->o_dx, r->dx.data(), T * sizeof(double));
+  memcpy(hp + r->o_dy, r->dy.data(), T * sizeof(double));
+  char *plan = s->d_arena + r->off_plan;
+  float *cube = reinterpret_cast<float *>(s->d_arena + r->off_cube);
+  cudaError_t e = cudaMemcpyAsync(plan, hp, r->plan_bytes, cudaMemcpyHostToDevice, s->s_in);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status + r->slot, 0, sizeof(int), s->s_in);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->d_arena + r->off_cube, r->host_in, r->cube_bytes, cudaMemcpyHostToDevice, s->s_in);
+  // the shift (Sect. 3.3.1) is done on the copy stream, piece by piece as the
+  // cube lands, so that it overlaps the copy as in a lone reduction
+  graphic::LineArgs a{};
+  a.p0 = reinterpret_cast<const double *>(plan + r->o_dx);
+  a.p1 = reinterpret_cast<const double *>(plan + r->o_dy);
+  a.n = r->n;
+  a.status = s->d_status + r->slot;
+  const size_t pb = graphic::line_params_bytes(graphic::SHIFT_X, r->n, T);
+  if (e == cudaSuccess) e = graphic::launch_line_params(graphic::SHIFT_X, a, T, plan + r->o_ptab, s->s_in);
+  if (e == cudaSuccess) e = graphic::launch_line_params(graphic::SHIFT_Y, a, T, plan + r->o_ptab + pb, s->s_in);
+  const int64_t NN = (int64_t)r->n * r->n;
+  const int64_t ch = std::max<int64_t>(1, std::min<int64_t>(T, ((int64_t)256 << 20) / (NN * (int64_t)sizeof(float))));
+  for (int64_t f0 = 0; f0 < T && e == cudaSuccess; f0 += ch) {
+    const int64_t nf = std::min<int64_t>(ch, T - f0);
+    e = cudaMemcpyAsync(cube + f0 * NN, r->host_in + f0 * NN, nf * NN * sizeof(float), cudaMemcpyHostToDevice, s->s_in);
+    graphic::LineArgs b = a;
+    b.in = cube + f0 * NN;
+    b.out = cube + f0 * NN;
+    b.in_fstride = b.out_fstride = NN;
+    b.p0 = a.p0 + f0;
+    b.p1 = a.p1 + f0;
+    b.lp_lines = 1;
+    b.lp_tab = plan + r->o_ptab + (size_t)f0 * (pb / T);
+    if (e == cudaSuccess) e = graphic::launch_line_pass(graphic::SHIFT_X, b, nf, s->s_in);
+    b.lp_tab = plan + r->o_ptab + pb + (size_t)f0 * (pb / T);
+    if (e == cudaSuccess) e = graphic::launch_line_pass(graphic::SHIFT_Y, b, nf, s->s_in);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_col, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(r->ev_in, s->s_in);
-  if (e == cudaSuccess) e = cudaLaunchHostFunc(s->s_in, on_wake, s);   // its shift may start
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(s->s_in, on_wake, s);   // its median may start
   return e == cudaSuccess ? GRAPHIC_OK : GRAPHIC_ERR_CUDA;
 }
 
@@ -331,8 +365,8 @@ void admit(graphic_server *s) {
 bool copied_in(const Req *r) { return cudaEventQuery(r->ev_in) == cudaSuccess; }
 
 // Work an iteration could do now: a request past its shift, or one whose
-// copy-in has completed; with nothing else pending, one still copying in
-// (the iteration then waits for it on the device).
+// copy-in and shift have completed; with nothing else pending, one still
+// copying in (the iteration then waits for it on the device).
 bool has_stage_work(const graphic_server *s) {
   bool admitted = false;
   for (const Req *r : s->active) {
@@ -350,32 +384,22 @@ void issue_iteration(graphic_server *s) {
   graphic_ctx *ctx = s->ctx[s->iters_issued & 1];
   Iter it;
   std::vector<graphic_batch_item> items;
-  std::vector<Req *> shift, adi, rot, col;
+  std::vector<Req *> adi, rot, col;
   bool others = false;
   for (Req *r : s->active) others |= (r->stage > ADMITTED && r->stage <= ROTATED) || (r->stage == ADMITTED && copied_in(r));
   for (Req *r : s->active) {
     switch (r->stage) {
-      case ADMITTED:
-        if (!others || copied_in(r)) shift.push_back(r);
+      case ADMITTED:   // copied in and shifted on the copy stream (or, with nothing else to do, soon)
+        if (!others || copied_in(r)) {
+          cudaStreamWaitEvent(s->s_comp, r->ev_in, 0);
+          adi.push_back(r);
+        }
         break;
       case SHIFTED: adi.push_back(r); break;
       case SUBTRACTED: rot.push_back(r); break;
       case ROTATED: col.push_back(r); break;
       default: break;
     }
-  }
-  for (Req *r : shift) {
-    cudaStreamWaitEvent(s->s_comp, r->ev_in, 0);
-    float *cube = reinterpret_cast<float *>(s->d_arena + r->off_cube);
-    graphic_batch_item b{};
-    b.in = cube;
-    b.out = cube;
-    b.n_frames = r->T;
-    b.n = r->n;
-    b.passes = GRAPHIC_PASS_SHIFT;
-    b.dx = r->dx.data();
-    b.dy = r->dy.data();
-    items.push_back(b);
   }
   for (Req *r : rot) {
     float *cube = reinterpret_cast<float *>(s->d_arena + r->off_cube);
@@ -391,12 +415,9 @@ void issue_iteration(graphic_server *s) {
   if (!items.empty()) {
     int rc = graphic::ctx_batch_async(ctx, items.data(), (int32_t)items.size(), s->mode);
     it.h_status = graphic::ctx_status_async(ctx);
-    if (rc != GRAPHIC_OK) {
-      for (Req *r : shift) fail_req(r, rc, graphic_last_error());
+    if (rc != GRAPHIC_OK)
       for (Req *r : rot) fail_req(r, rc, graphic_last_error());
-    }
-    it.batch = shift;
-    it.batch.insert(it.batch.end(), rot.begin(), rot.end());
+    it.batch = rot;
     std::lock_guard<std::mutex> lk(s->mu);
     s->st.batch_launches++;
     s->st.batch_items += (int64_t)items.size();
@@ -425,6 +446,8 @@ void issue_iteration(graphic_server *s) {
     a.T = (int)r->T;
     a.n = r->n;
     a.in_fs = a.out_fs = (long long)r->n * r->n;
+    a.perm_id = 1;
+    for (int64_t t = 0; t < r->T && a.perm_id; t++) a.perm_id = r->ap.perm[t] == (int)t;
     a.n_ann = r->n_ann;
     if (graphic::launch_adi_median(a, s->s_comp) != cudaSuccess) fail_req(r, GRAPHIC_ERR_CUDA, "median PSF kernel");
   }
@@ -446,7 +469,6 @@ void issue_iteration(graphic_server *s) {
       r->gpu_done.store(true);
     }
   }
-  for (Req *r : shift) r->stage = SHIFTED;
   for (Req *r : adi) r->stage = SUBTRACTED;
   for (Req *r : rot) r->stage = ROTATED;
   for (Req *r : col) r->stage = FINISHING;
@@ -600,7 +622,13 @@ int graphic_server_submit(graphic_server *s, const graphic_request *rq, int64_t 
   o = align16(o + r->ap.evq.size() * sizeof(uint32_t));
   r->o_groups = o;
   o = align16(o + r->ap.groups.size() * sizeof(int));
+  r->o_dx = o;
+  o = align16(o + T * sizeof(double));
+  r->o_dy = o;
+  o = align16(o + T * sizeof(double));
   r->plan_bytes = o;
+  r->o_ptab = o;
+  o = align16(o + 2 * graphic::line_params_bytes(graphic::SHIFT_X, r->n, T));
   r->plan_dev_bytes = o;
   r->stage_bytes = r->plan_bytes + r->out_bytes;
   std::lock_guard<std::mutex> lk(s->mu);
