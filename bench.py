@@ -17,7 +17,8 @@ mixed sizes through the batch executors and the autotuner), serve (the
 serving loop alone), precision (512 x 1024^2 shift + rotation per
 arithmetic, tensor-core variants), prep (master skies, sky subtraction, bad
 pixels), register (centroid + Moffat fit of 2000 raw frames), photometry
-(the inject / recentre / bin / reduce / aperture protocol).  --impl
+(the inject / recentre / bin / reduce / aperture protocol), median /
+collapse (one step of the reduction alone, for kernel captures).  --impl
 reference times the CPU oracle on the host cores.
 """
 from __future__ import annotations
@@ -1092,6 +1093,59 @@ def run_uneven(args, rank, world, local_rank):
     return 0
 
 
+def run_stage(args, rank, world, local_rank):
+    """One step of the reduction alone on the survey recipe cube (resident
+    on the device): `median` = the median PSF subtraction, `collapse` = the
+    median collapse.  For kernel captures of a single step."""
+    import torch
+    from paper_1510_04331_gb300 import graphic
+
+    torch.cuda.set_device(local_rank)
+    d = make_workload("survey", args.frames, args.n)
+    T, n = d.cube.shape[0], d.cube.shape[1]
+    x = torch.from_numpy(d.cube).cuda()
+    work = torch.empty_like(x) if args.workload == "median" else None
+    img = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ctx = graphic.Context(local_rank)
+
+    def step():
+        if args.workload == "median":
+            ctx.graphic_adi_subtract(x, d.parang, d.fwhm, d.n_fwhm, d.edges, out=work)
+        else:
+            ctx.graphic_collapse_median(x, out=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    ctx.profile(True)
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    med = statistics.median(ms)
+    nbytes = (2 if args.workload == "median" else 1) * T * n * n * 4
+    hbm, src = peaks()
+    line = {
+        "metric": f"ms per call, {args.workload} step alone", "value": med, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": med, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc("survey", d) + f"; {args.workload} step only", "frames": T, "n": n},
+        "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k, v in prof.items() if v[1]},
+        "hbm": {"algorithmic_bytes": nbytes, "gbs": nbytes / (med / 1e3) / 1e9,
+                "frac": nbytes / (med / 1e3) / 1e9 / hbm, "peak_source": src},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1099,7 +1153,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="survey",
-                    choices=sorted(WORKLOADS) + ["uneven", "serve", "precision", "prep", "register", "photometry"])
+                    choices=sorted(WORKLOADS) + ["uneven", "serve", "precision", "prep", "register", "photometry",
+                                                 "median", "collapse"])
     ap.add_argument("--no-tune", action="store_true", help="uneven workload: skip the autotuner")
     ap.add_argument("--frames", type=int, default=None, help="override the workload's frame count")
     ap.add_argument("--n", type=int, default=None, help="override the workload's frame side")
@@ -1124,6 +1179,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "uneven":
         return run_uneven(args, rank, world, local_rank)
+    if args.workload in ("median", "collapse"):
+        return run_stage(args, rank, world, local_rank)
     if args.workload == "precision":
         return run_precision(args, rank, world, local_rank)
     if args.workload == "prep":

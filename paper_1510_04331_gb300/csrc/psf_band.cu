@@ -57,7 +57,7 @@ namespace {
 
 constexpr int PPC = 4;     // pixels (warps) per CTA
 constexpr int KS = 4;      // band_prep_kernel: words per frame row of the keys (one 16-byte copy per frame)
-constexpr int SWK = 8;     // queries per lockstep sweep block
+constexpr int SWK = 4;     // queries per lockstep sweep block (4 measured faster than 8: smaller blocks, more CTAs)
 constexpr int NCLASS = 7;  // group classes: 0 = no pixel in an annulus, then bit map words 1, 2, 4, ..., 32
 constexpr int kClassW[NCLASS] = {0, 1, 2, 4, 8, 16, 32};
 
@@ -399,18 +399,20 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
 
 // Shared memory: per warp skeys[NB] u32, blev[NB] u32, bm[NB] u32 (bit map,
 // word wd of lane c at wd * 32 + c), blpos[NB] u16, belowc[nwt + 1] uint2
-// (BELOW word, BELOW frames before it); per CTA the staged gate of the
-// group's first annulus [T] u32 (L | R << 16) and the value / residual blocks.
+// (BELOW word, BELOW frames before it); per CTA the value / residual blocks.
+// The gates (L_i, R_i) are read through L1 (a few KB per annulus, shared by
+// every CTA of the annulus): measured faster than staging them, which cost
+// resident CTAs.
 __host__ __device__ inline size_t sweep_warp_bytes(int NB, int nwt) {
   return (size_t)NB * 12 + al16((size_t)NB * 2) + al16((size_t)(nwt + 1) * 8);
 }
 constexpr size_t kBlockBytes = (size_t)SWK * 32 * 16;   // [SWK][32 lanes] float4
 __host__ __device__ inline size_t sweep_smem_bytes(int NB, int nwt, int T) {
-  return PPC * sweep_warp_bytes(NB, nwt) + al16((size_t)T * 4) + 3 * kBlockBytes;
+  return PPC * sweep_warp_bytes(NB, nwt) + 3 * kBlockBytes;
 }
 
 template <int WC>
-__global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) band_sweep_kernel(const BandArgs B) {
+__global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) band_sweep_kernel(const BandArgs B) {
   extern __shared__ __align__(16) unsigned char ssm[];
   constexpr int NB = 32 * WC;
   const AdiArgs &a = B.a;
@@ -425,10 +427,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
   uint16_t *blpos = reinterpret_cast<uint16_t *>(bm + NB);
   uint2 *belowc = reinterpret_cast<uint2 *>(wb + (size_t)NB * 12 + al16((size_t)NB * 2));
   unsigned char *cb_ = ssm + PPC * sweep_warp_bytes(NB, nwt);
-  uint32_t *gate_all = reinterpret_cast<uint32_t *>(cb_);                               // [T]
-  float4 *vbuf = reinterpret_cast<float4 *>(cb_ + al16((size_t)T * 4));                // [2][SWK][32]
-  float *obuf = reinterpret_cast<float *>(cb_ + al16((size_t)T * 4) + 2 * kBlockBytes);   // [SWK][32][4]
-  __shared__ int gate_ann[1];
+  float4 *vbuf = reinterpret_cast<float4 *>(cb_);                                      // [2][SWK][32]
+  float *obuf = reinterpret_cast<float *>(cb_ + 2 * kBlockBytes);                       // [SWK][32][4]
 
   // ---- this pixel's band data -------------------------------------------
   const char *slot = B.slots + ((size_t)blockIdx.x * PPC + w) * B.slot_bytes;
@@ -462,26 +462,6 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
       carry += __shfl_sync(FULL, inc, 31);
     }
   }
-  // ---- gate of the group's first annulus, staged ---------------------------
-  if (threadIdx.x == 0) gate_ann[0] = -1;
-  __syncthreads();
-  if (lane == 0 && ann >= 0) atomicCAS(&gate_ann[0], -1, ann);
-  __syncthreads();
-  {
-    const int an = gate_ann[0];
-    if (an >= 0) {
-      const int2 *lr2 = reinterpret_cast<const int2 *>(a.lr + (size_t)an * T * 2);
-      for (int s = threadIdx.x; s < T; s += 32 * PPC) {
-        const int2 v = __ldg(&lr2[s]);
-        gate_all[s] = (uint32_t)v.x | ((uint32_t)v.y << 16);
-      }
-    }
-  }
-  __syncthreads();
-  // this pixel's gate: the staged copy, or global memory (a second annulus
-  // in one group: groups that straddle an annulus edge)
-  const int gsel = gate_ann[0] == ann ? 0 : -1;
-  const int goff = 0;
   const int2 *gate_g = reinterpret_cast<const int2 *>(a.lr + (size_t)(ann < 0 ? 0 : ann) * T * 2);
 
   const int C = (T + 31) / 32;
@@ -583,14 +563,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 6 : (WC == 16 ? 4 : 2)) 
           }
           ne = min(na, nq);
         }
-        uint32_t g;
-        if (gsel >= 0) {
-          g = gate_all[goff + i];
-        } else {
-          const int2 v = __ldg(&gate_g[i]);
-          g = (uint32_t)v.x | ((uint32_t)v.y << 16);
-        }
-        const int Li = (int)(g & 0xffffu), Ri = (int)(g >> 16);
+        const int2 gv = __ldg(&gate_g[i]);
+        const int Li = gv.x, Ri = gv.y;
         // BELOW members of S_i: BELOW frames before L_i and from R_i on
         const uint2 ul = belowc[Li >> 5], ur = belowc[Ri >> 5];
         const int bl = (int)ul.y + __popc(ul.x & ((1u << (Li & 31)) - 1u));
@@ -789,8 +763,9 @@ cudaError_t launch_adi_band(const AdiArgs &a, cudaStream_t st, int *launched) {
     b.NB = 32 * kClassW[k];
     b.nwt = nwt;
     b.slot_bytes = Slot(b.NB, nwt).bytes;
-    // candidates: the band and the spill of its two end bins, at most T
-    b.cap = std::min(T, std::max(2 * b.NB, 64));
+    // candidates: the band (more than NB / 2 ranks) and the spill of its two
+    // end bins (a few dozen keys), at most T
+    b.cap = std::min(T, b.NB + std::max(64, b.NB / 4));
     const size_t psmem = prep_smem_bytes(T, b.cap, nwt);
     cudaError_t e = cudaFuncSetAttribute(band_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
