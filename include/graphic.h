@@ -225,7 +225,7 @@ int graphic_rotate_noalloc(const float *in, float *out, int64_t n_frames, int32_
 /* ---- image-quality pre-processing (Sect. 3.2) --------------------------------- */
 
 /*
- * Master sky (Sect. 3.2, "Master sky"): sky(p) = median over the n_frames
+ * Master sky (Sect. 3.2, master sky): sky(p) = median over the n_frames
  * frames of the values in[t](p) that are finite and lie outside frame t's
  * star mask, i.e. not within mask_r pixels of (mask_x[t], mask_y[t]) (x =
  * column, y = row; mask_x = mask_y = NULL: no mask).  Masked regions may
@@ -246,7 +246,7 @@ int graphic_sky_subtract(graphic_ctx *ctx, const float *in, float *out, int64_t 
                          const float *skies, int32_t n_skies, const double *frame_times, const double *sky_times);
 
 /*
- * Bad pixel map (Sect. 3.2, "Bad pixel correction"): map[p] = 1 when
+ * Bad pixel map (Sect. 3.2, bad pixel correction): map[p] = 1 when
  * |ref[p] - median(ref)| > C sigma, sigma the population standard deviation
  * of the n x n values of ref (FP64), the median by the rule above (FP32),
  * the comparison in FP64; else 0.  ref (a master dark or sky) and map

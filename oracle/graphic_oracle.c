@@ -11,13 +11,15 @@
  *     the Fourier transform definitions);
  *   - the Fourier sub-pixel shift of a zero-padded frame as ONE 2-D transform
  *     multiplied by the separable phasor (Sect. 3.3.1, shift theorem, 2-D
- *     phasor, "at least double sized frames");
+ *     phasor, frames padded to twice their size or more);
  *   - the three-shear Fourier rotation (Sect. 3.4, shear decomposition and
  *     the Fourier form of each shear, double sized frame);
  *   - the angle gate, the optional maximum time separation t_max, and the
  *     per-frame median PSF subtraction (Sect. 3.3, parallactic angle /
- *     reference-frame conditions, "without any combination coefficients");
- *   - the final median collapse (Sect. 3.4, "merge all the frames").
+ *     reference-frame conditions; the median is subtracted as it is, with no
+ *     fitted weights);
+ *   - the final median collapse (Sect. 3.4, the derotated frames combined
+ *     into one image by their median).
  *
  * Conventions where the paper is silent or garbled (also listed in the
  * design notes): shift(d) moves content by +d (out(x) = in(x - d)); signed
@@ -608,7 +610,7 @@ int oracle_reduce(const double *cube, double *work, long long T, int N, const do
 /* Image-quality pre-processing (Sect. 3.2)                               */
 /* ---------------------------------------------------------------------- */
 
-/* Exported: master sky (Sect. 3.2, "Master sky"): per pixel the median over
+/* Exported: master sky (Sect. 3.2, master sky): per pixel the median over
  * the T frames of the values that are finite and lie outside the star mask
  * of their frame (distance to (mask_x[t], mask_y[t]) below mask_r, pixel
  * coordinates x = column, y = row; mask_x == NULL: no mask).  A pixel with
@@ -657,7 +659,7 @@ int oracle_sky_subtract_f32(const float *cube, float *out, long long T, int N, c
     return 0;
 }
 
-/* Exported: bad pixel map (Sect. 3.2, "Bad pixel correction"): map[p] = 1
+/* Exported: bad pixel map (Sect. 3.2, bad pixel correction): map[p] = 1
  * when |ref[p] - median(ref)| > C sigma, sigma the population standard
  * deviation of ref (FP64), the median of the N x N values in FP32 (two
  * middle values averaged for an even count), the comparison in FP64. */
@@ -735,8 +737,8 @@ int oracle_bad_pixel_fix_f32(float *cube, long long T, int N, const unsigned cha
 /* Registration (Sect. 3.1): centroid patch search and Moffat fit          */
 /* ---------------------------------------------------------------------- */
 
-/* Exported: centroid search of one frame (Sect. 3.1, "searches for a patch
- * of contiguous pixels above a given threshold value"): the seed is the
+/* Exported: centroid search of one frame (Sect. 3.1, a connected group of
+ * pixels above a threshold): the seed is the
  * brightest pixel (the first in row-major order on a tie); the patch is the
  * 8-connected set of pixels with value > thresh reachable from the seed
  * inside the box of half-size R around it (clipped to the frame).  The
@@ -943,8 +945,8 @@ double oracle_moffat_fwhm(double alpha, double beta)
 /* Photometric-accuracy and binning experiments (Sect. 4.2, 4.3)           */
 /* ---------------------------------------------------------------------- */
 
-/* Exported: median binning (Sect. 4.3, "combining each set of ten ... frames
- * into a single median frame"; the quick-look binning of Sect. 3.1): group g
+/* Exported: median binning (Sect. 4.3, each run of ten frames replaced by
+ * its median frame; the quick-look binning of Sect. 3.1): group g
  * holds frames [g B, min(T, (g + 1) B)) (the last group may be shorter) and
  * out[g](p) is the median of its values at pixel p, by the median rule of
  * the collapse (sort, middle value, mean of the two middle values in FP32

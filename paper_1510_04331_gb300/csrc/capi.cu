@@ -587,8 +587,8 @@ AdiOffsets add_adi_plan(PlanBuilder &pb, const AdiPlanHost &ap, int64_t T) {
 int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t n, const int *p_perm,
                     const int *p_lr, const double *p_edge2, const int *p_band, int wmax, int n_ann,
                     const int *p_ab, const uint32_t *p_evq, const int *p_groups, const std::vector<int> &class_off,
-                    char *band_scratch, size_t band_scratch_cap, long long in_fs, long long out_fs,
-                    bool perm_id) {
+                    int gen_off, int gen_n, char *band_scratch, size_t band_scratch_cap, long long in_fs,
+                    long long out_fs, bool perm_id) {
   AdiArgs a{};
   a.perm_id = perm_id ? 1 : 0;
   a.in_fs = in_fs ? in_fs : (long long)n * n;
@@ -597,6 +597,9 @@ int enqueue_adi_raw(graphic_ctx *c, const float *in, float *out, int64_t T, int3
   a.evq = p_evq;
   a.groups = p_groups;
   for (int k = 0; k < 8; k++) a.class_off[k] = k < (int)class_off.size() ? class_off[k] : 0;
+  a.gen_list = gen_off >= 0 ? 1 : 0;
+  a.gen_off = gen_off;
+  a.gen_n = gen_n;
   a.band_scratch = band_scratch;
   a.in = in;
   a.out = out;
@@ -658,7 +661,8 @@ int enqueue_adi(graphic_ctx *c, const float *in, float *out, int64_t T, int32_t 
   return enqueue_adi_raw(c, in, out, T, n, at<int>(c, o.perm), at<int>(c, o.lr), at<double>(c, o.e2),
                          at<int>(c, o.band), ap.wmax, (int)ap.edge2.size() - 1,
                          ap.ab.empty() ? nullptr : at<int>(c, o.ab), at<uint32_t>(c, o.evq), at<int>(c, o.groups),
-                         ap.class_off, c->d_bscratch, c->bscratch_bytes, in_fs, out_fs, perm_id);
+                         ap.class_off, ap.gen_off, ap.gen_n, c->d_bscratch, c->bscratch_bytes, in_fs, out_fs,
+                         perm_id);
 }
 
 // Full reduction of the device cube `in` (work may equal in).  With host_in,

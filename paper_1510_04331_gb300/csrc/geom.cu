@@ -538,6 +538,65 @@ __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *
   __syncwarp();
 }
 
+// The shift of one line pair held in registers (v[m] = element lane + 32 m,
+// packed as line a + i line b): forward transform, spectrum separation and
+// per-line phasors (Sect. 3.3.1 shift theorem; lines a and b shifted by
+// their own amounts unless SAME_D), inverse transform.  On return v[r] is
+// conj(y) at element lane + 32 r.  buf: the warp's exchange buffer.
+template <int KIND>
+__device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *buf, const float2 *__restrict__ tw,
+                                           const LineParam &la, const LineParam &lb) {
+  constexpr int M = 1024;
+  constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
+  fft1024_warp(v, lane, buf, tw);
+
+  // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
+  if constexpr (!SAME_D) {
+#pragma unroll
+    for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
+    __syncwarp();
+  }
+  const float inv_m = 1.0f / (float)M;
+  // phasors H_k = exp(-i 2 pi ks delta), ks the signed bin: exact anchors at
+  // r = 0, 8, 16, 24, a product with exp(-i 2 pi 32 delta) in between
+  const float2 sa = phase_at(la, 32);
+  const float2 sb = SAME_D ? sa : phase_at(lb, 32);
+  float2 ha, hb;
+#pragma unroll
+  for (int r = 0; r < 32; r++) {
+    const int k = lane + 32 * r;
+    if ((r & 7) == 0) {
+      const int ks = (r < 16) ? k : k - M;
+      ha = phase_at(la, ks);
+      hb = SAME_D ? ha : phase_at(lb, ks);
+    } else {
+      ha = cmul(ha, sa);
+      hb = SAME_D ? ha : cmul(hb, sb);
+    }
+    float2 ua = ha, ub = hb;
+    if (r == 16 && lane == 0) {   // Nyquist bin
+      ua = make_float2(la.cnyq, 0.f);
+      ub = make_float2(lb.cnyq, 0.f);
+    }
+    const float2 z = v[r];
+    float2 vk;
+    if constexpr (SAME_D) {
+      vk = cmul(z, ua);
+    } else {
+      const float2 zm = buf[pad32((M - k) & (M - 1))];
+      const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+      const float2 P = cmul(A, ua), Q = cmul(B, ub);
+      vk = make_float2(P.x - Q.y, P.y + Q.x);
+    }
+    v[r] = make_float2(vk.x * inv_m, -vk.y * inv_m);   // conj(V) / m
+  }
+  __syncwarp();
+
+  // ---- inverse: the same stages on conj(V)/m; y = conj(result) ------------
+  fft1024_warp(v, lane, buf, tw);
+}
+
 // Line pairs (warps) per CTA: 4 (column passes move 32-byte row pieces of
 // their 8 adjacent columns; 8 pairs per CTA with 64-byte pieces measured
 // slower: shift columns 2.46 -> 2.70 ms per survey step).  Register budget
@@ -683,55 +742,7 @@ __global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) li
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
   }
   if (COLS || RCOLS) __syncwarp();   // buf is the FFT's exchange buffer from here on
-  fft1024_warp(v, lane, buf, tw);
-
-  // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
-  if constexpr (!SAME_D) {
-#pragma unroll
-    for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
-    __syncwarp();
-  }
-  const LineParam &la = lp[p][0];
-  const LineParam &lb = lp[p][SAME_D ? 0 : 1];
-  const float inv_m = 1.0f / (float)M;
-  // phasors H_k = exp(-i 2 pi ks delta), ks the signed bin: exact anchors at
-  // r = 0, 8, 16, 24, a product with exp(-i 2 pi 32 delta) in between
-  const float2 sa = phase_at(la, 32);
-  const float2 sb = SAME_D ? sa : phase_at(lb, 32);
-  float2 ha, hb;
-#pragma unroll
-  for (int r = 0; r < 32; r++) {
-    const int k = lane + 32 * r;
-    if ((r & 7) == 0) {
-      const int ks = (r < 16) ? k : k - M;
-      ha = phase_at(la, ks);
-      hb = SAME_D ? ha : phase_at(lb, ks);
-    } else {
-      ha = cmul(ha, sa);
-      hb = SAME_D ? ha : cmul(hb, sb);
-    }
-    float2 ua = ha, ub = hb;
-    if (r == 16 && lane == 0) {   // Nyquist bin
-      ua = make_float2(la.cnyq, 0.f);
-      ub = make_float2(lb.cnyq, 0.f);
-    }
-    const float2 z = v[r];
-    float2 vk;
-    if constexpr (SAME_D) {
-      vk = cmul(z, ua);
-    } else {
-      const float2 zm = buf[pad32((M - k) & (M - 1))];
-      const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-      const float2 P = cmul(A, ua), Q = cmul(B, ub);
-      vk = make_float2(P.x - Q.y, P.y + Q.x);
-    }
-    v[r] = make_float2(vk.x * inv_m, -vk.y * inv_m);   // conj(V) / m
-  }
-  __syncwarp();
-
-  // ---- inverse: the same stages on conj(V)/m; y = conj(result) ------------
-  fft1024_warp(v, lane, buf, tw);
+  w32_filter<KIND>(v, lane, buf, tw, lp[p][0], lp[p][SAME_D ? 0 : 1]);
   if constexpr (COLS) {
     // through the per-pair buffers, then row by row as 16-byte pieces
     __syncwarp();

@@ -65,10 +65,14 @@ struct AdiPlanHost {
   // band path (plan_band_path): event queries [A][T] (a_s | b_s << 16: frame s
   // is outside the reference set of the queries a_s <= i < b_s), the 4-pixel
   // groups of the band path class after class (0: no pixel in an annulus;
-  // then bit map widths 1, 2, 4, 8, 16, 32 words), class offsets [8]
+  // then bit map widths 1, 2, 4, 8, 16, 32 words), class offsets [8]; after
+  // the classes, from gen_off on, the gen_n 8-pixel blocks (index p / 8)
+  // with a pixel of an annulus that has no band: the general path's grid
+  // (gen_off < 0: every block)
   std::vector<uint32_t> evq;
   std::vector<int> groups;
   std::vector<int> class_off;
+  int gen_off = -1, gen_n = 0;
 };
 // Returns GRAPHIC_OK, or an error code (last error set) for times that are
 // not monotone in the angle order or a t_max that is not > 0.
@@ -181,6 +185,9 @@ struct AdiArgs {
   const uint32_t *evq;   // [A][T] device
   const int *groups;     // device, class after class
   int class_off[8];      // host copy of AdiPlanHost::class_off
+  int gen_list;          // 1: the general path runs on the gen_n blocks listed at groups + gen_off
+                         // (AdiPlanHost::gen_off, gen_n); 0: on every 8-pixel block
+  int gen_off, gen_n;
   char *band_scratch;    // device scratch of band_scratch_cap bytes (at least one group's tables)
   size_t band_scratch_cap;
   // optional hook around each group of launches (profiling): mark(user,
@@ -189,8 +196,8 @@ struct AdiArgs {
   void (*mark)(void *user, int kind, int begin);
   void *mark_user;
 };
-// *launched (may be null) receives the number of kernels launched (1 to 3:
-// general path, band path W <= 16, band path W = 32).
+// *launched (may be null) receives the number of kernels launched (the
+// general path when it has blocks, then the band path's launches).
 cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched = nullptr);
 // psf_band.cu: the band path's launches (zero groups, then per class the
 // preparation and the sweep); *launched is incremented per kernel

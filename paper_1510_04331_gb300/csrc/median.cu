@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
     orv |= __shfl_xor_sync(FULL, orv, o);
     andv &= __shfl_xor_sync(FULL, andv, o);
   }
-  if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
+  const bool anybad = __any_sync(FULL, bad);
+  if (anybad && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
   __syncwarp();
   const uint32_t varying = orv ^ andv;
 
@@ -221,19 +222,15 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
 }
 
 // Median collapse of unmasked cubes that fit shared memory.  Per pixel
-// (one warp): the keys in shared memory (odd row stride, conflict-free), a
-// 256-bin histogram linear in value between the pixel's extremes locates
-// the bins of the two middle ranks; one pass copies the keys of those bins
-// (usually one bin of a few dozen keys) into the row padding words, and the
-// middle ranks are read off by counting within that list.  A list longer
-// than its capacity (heavy outliers, many equal values) falls back to exact
-// radix selects of the two middle ranks over all keys.
-__device__ __forceinline__ int vbin_c(uint32_t k, float v0, float scale) {
-  const float x = (key2f(k) - v0) * scale;
-  const int b = (int)x;   // x >= 0, or NaN (inf * 0) which converts to 0
-  return b < 255 ? b : 255;
-}
-
+// (one warp): the values in shared memory (odd row stride, conflict-free).
+// A 256-bin histogram linear in value over the interquartile range of 32
+// sampled frames (values outside it counted below or ignored above), filled
+// in one pass over the raw values, locates the bins of the two middle
+// ranks; a second pass copies the total-order keys of those bins (a few
+// values) into the row padding words, and the middle ranks are read off by
+// counting within that list.  A middle rank outside the range, a list
+// longer than its capacity (many equal values) or a non-finite value falls
+// back to exact radix selects of the two middle ranks over all keys.
 __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
   uint32_t *hist_all = csm;                       // [COL_PPC][512]
@@ -249,37 +246,59 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
   cp_async_wait_all();
   __syncthreads();
   uint32_t *hist = hist_all + w * 512;
-  uint32_t *kw = keys_all + w;   // key of frame t: kw[t * COL_KS]
+  uint32_t *kw = keys_all + w;   // value (then key) of frame t: kw[t * COL_KS]
+  const uint32_t k0 = (uint32_t)((T - 1) / 2);
+  const bool even = (T & 1) == 0;
+  const uint32_t k1 = even ? k0 + 1 : k0;
+  // histogram range: the interquartile range of 32 frames sampled evenly in
+  // time (bitonic sort across the warp; the min and max of the sample when
+  // the quartiles coincide).  The median lies between the sample's quartiles
+  // unless fewer than 9 or more than 23 of the 32 sampled values fall below
+  // it (well under 1 % of pixels when frames vary independently); then, as
+  // for a range the sample missed, the exact path below takes over.
+  float lo = 0.f, scale = 0.f;
+  if (T >= 32) {
+    float x = __uint_as_float(kw[(int)(((long long)lane * T) >> 5) * COL_KS]);
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int d = k >> 1; d > 0; d >>= 1) {
+        const float y = __shfl_xor_sync(FULL, x, d);
+        const bool up = (lane & k) == 0, low = (lane & d) == 0;
+        x = (up == low) ? fminf(x, y) : fmaxf(x, y);
+      }
+    }
+    float qlo = __shfl_sync(FULL, x, 8), qhi = __shfl_sync(FULL, x, 23);
+    if (!(qhi > qlo)) {
+      qlo = __shfl_sync(FULL, x, 0);
+      qhi = __shfl_sync(FULL, x, 31);
+    }
+    const float sc = 256.f / (qhi - qlo);
+    if (qhi > qlo && sc <= 3.4e38f) {   // finite range and scale
+      lo = qlo;
+      scale = sc;
+    }
+  }
+  // one pass over the raw values: x = (v - lo) scale is monotone in v;
+  // x < 0 counts below the range, [0, 256) takes bin (int) x, the rest is
+  // above.  (scale = 0 puts every finite value in bin 0.)  The finiteness
+  // check rides along.
+#pragma unroll
+  for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0u;
+  __syncwarp();
   bool bad = false;
-  uint32_t kmin = 0xffffffffu, kmax = 0u, orv = 0u, andv = 0xffffffffu;
+  uint32_t nb = 0;
 #pragma unroll 4
   for (int t = lane; t < T; t += 32) {
     const float v = __uint_as_float(kw[t * COL_KS]);
     bad |= !isfinite(v);
-    const uint32_t k = f2key(v);
-    kw[t * COL_KS] = k;
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
-    orv |= k;
-    andv &= k;
+    const float xv = (v - lo) * scale;
+    if (xv < 0.f) nb++;
+    else if (xv < 256.f) atomicAdd(&hist[(int)xv], 1u);
   }
-  kmin = __reduce_min_sync(FULL, kmin);
-  kmax = __reduce_max_sync(FULL, kmax);
-  orv = __reduce_or_sync(FULL, orv);
-  andv = __reduce_and_sync(FULL, andv);
-  if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
-  const uint32_t k0 = (uint32_t)((T - 1) / 2);
-  const bool even = (T & 1) == 0;
-  const uint32_t k1 = even ? k0 + 1 : k0;
-  // histogram linear in value
-  const float v0 = key2f(kmin);
-  const float range = key2f(kmax) - v0;
-  const float scale = (range > 0.f) ? 256.f / range : 0.f;
-#pragma unroll
-  for (int b = 0; b < 8; b++) hist[lane * 8 + b] = 0u;
-  __syncwarp();
-#pragma unroll 4
-  for (int t = lane; t < T; t += 32) atomicAdd(&hist[vbin_c(kw[t * COL_KS], v0, scale)], 1u);
+  const bool anybad = __any_sync(FULL, bad);
+  if (anybad && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
+  const uint32_t nbelow = __reduce_add_sync(FULL, nb);
   __syncwarp();
   uint32_t h[8], hs = 0;
 #pragma unroll
@@ -293,55 +312,61 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     const uint32_t tt = __shfl_up_sync(FULL, inc, o);
     if (lane >= o) inc += tt;
   }
-  // bins of ranks k0 and k1 and the keys below them
-  int bin[2];
-  uint32_t bel[2];
+  const uint32_t inside = __shfl_sync(FULL, inc, 31);
+  // bins of ranks k0 and k1 (ranks within the range: k - nbelow) and the
+  // values below them; a rank outside the range takes the exact path
+  const bool in_range = k0 >= nbelow && k1 - nbelow < inside;
+  int bin[2] = {0, 0};
+  uint32_t bel[2] = {0u, 0u};
+  if (in_range) {
 #pragma unroll
-  for (int q = 0; q < 2; q++) {
-    const uint32_t r = q ? k1 : k0;
-    const unsigned ball = __ballot_sync(FULL, inc > r);
-    const int L = ball ? __ffs(ball) - 1 : 31;
-    int bb = 0;
-    uint32_t be = 0;
-    if (lane == L) {
-      uint32_t acc = inc - hs;
-      bool done = false;
+    for (int q = 0; q < 2; q++) {
+      const uint32_t r = (q ? k1 : k0) - nbelow;
+      const unsigned ball = __ballot_sync(FULL, inc > r);
+      const int L = __ffs(ball) - 1;
+      int bb = 0;
+      uint32_t be = 0;
+      if (lane == L) {
+        uint32_t acc = inc - hs;
+        bool done = false;
 #pragma unroll
-      for (int b = 0; b < 8; b++) {
-        if (!done && acc + h[b] > r) {
-          bb = lane * 8 + b;
-          be = acc;
-          done = true;
+        for (int b = 0; b < 8; b++) {
+          if (!done && acc + h[b] > r) {
+            bb = lane * 8 + b;
+            be = acc;
+            done = true;
+          }
+          acc += h[b];
         }
-        acc += h[b];
       }
+      bin[q] = __shfl_sync(FULL, bb, L);
+      bel[q] = __shfl_sync(FULL, be, L) + nbelow;
     }
-    bin[q] = __shfl_sync(FULL, bb, L);
-    bel[q] = __shfl_sync(FULL, be, L);
   }
-  const int nlist = (int)(bel[1] + hist[bin[1]] - bel[0]);
+  const int nlist = in_range ? (int)(bel[1] + hist[bin[1]] - bel[0]) : 0x7fffffff;
   // the list lives in the padding word of rows [w cap, (w + 1) cap)
   const int cap = min(T / COL_PPC, 256);
   float med;
-  if (nlist <= cap) {
+  if (!anybad && nlist <= cap) {
     uint32_t *cbuf = keys_all + (size_t)w * cap * COL_KS + (COL_KS - 1);   // element j at cbuf[j * COL_KS]
     const unsigned lt = (1u << lane) - 1u;
     int len = 0;
-    // four 32-frame rounds per step: their loads and bins are independent
+    // four 32-frame rounds per step: their loads and bins are independent;
+    // the list holds total-order keys
     for (int t0 = 0; t0 < T; t0 += 128) {
-      uint32_t k[4];
+      float v[4];
       bool in[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int t = t0 + 32 * u + lane;
-        k[u] = t < T ? kw[t * COL_KS] : 0u;
-        const int b = vbin_c(k[u], v0, scale);
-        in[u] = t < T && b >= bin[0] && b <= bin[1];
+        v[u] = t < T ? __uint_as_float(kw[t * COL_KS]) : 0.f;
+        const float xv = (v[u] - lo) * scale;
+        in[u] = t < T && xv >= 0.f && xv < 256.f && (unsigned)((int)xv - bin[0]) <= (unsigned)(bin[1] - bin[0]);
       }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const unsigned mm = __ballot_sync(FULL, in[u]);
-        if (in[u]) cbuf[(len + __popc(mm & lt)) * COL_KS] = k[u];
+        if (in[u]) cbuf[(len + __popc(mm & lt)) * COL_KS] = f2key(v[u]);
         len += __popc(mm);
       }
     }
@@ -364,6 +389,17 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     f1 = __reduce_min_sync(FULL, f1);
     med = even ? (key2f(f0) + key2f(f1)) * 0.5f : key2f(f0);
   } else {
+    // exact: keys in place, then radix selects of the two middle ranks
+    uint32_t orv = 0u, andv = 0xffffffffu;
+    for (int t = lane; t < T; t += 32) {
+      const uint32_t k = f2key(__uint_as_float(kw[t * COL_KS]));
+      kw[t * COL_KS] = k;
+      orv |= k;
+      andv &= k;
+    }
+    orv = __reduce_or_sync(FULL, orv);
+    andv = __reduce_and_sync(FULL, andv);
+    __syncwarp();
     uint32_t Klo, Khi, clo, chi;
     band_select2<COL_KS>(kw, T, k0, k1, orv ^ andv, andv, hist, hist + 256, lane, Klo, clo, Khi, chi);
     med = even ? (key2f(Klo) + key2f(Khi)) * 0.5f : key2f(Klo);
@@ -409,7 +445,7 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
 
   const int T = a.T;
   const long long NN = (long long)a.n * a.n;
-  const long long p0 = (long long)blockIdx.x * 8;
+  const long long p0 = (long long)(a.gen_list ? __ldg(&a.groups[a.gen_off + blockIdx.x]) : (int)blockIdx.x) * 8;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = tcap / 32;   // bitmap words per lane column
 
@@ -706,7 +742,7 @@ cudaError_t launch_adi_median(const AdiArgs &a, cudaStream_t st, int *launched) 
   if (a.mark) a.mark(a.mark_user, 0, 1);
   cudaError_t e = launch_adi_general(a, st, tcap);
   if (a.mark) a.mark(a.mark_user, 0, 0);
-  nl += (e == cudaSuccess);
+  nl += (e == cudaSuccess && (!a.gen_list || a.gen_n > 0));
   if (e != cudaSuccess || a.wmax == 0) return e;
   return launch_adi_band(a, st, &nl);
 }
@@ -715,9 +751,14 @@ cudaError_t launch_adi_general(const AdiArgs &a, cudaStream_t st, int tcap) {
   const long long NN = (long long)a.n * a.n;
   const size_t smem = (size_t)8 * 256 * sizeof(uint32_t) +
                       (size_t)8 * tcap * (2 * sizeof(uint32_t) + 2 * sizeof(uint16_t)) + (size_t)tcap * sizeof(uint16_t);
+  // the plan lists the blocks with a pixel of an annulus without a band
+  // (every other block would read its annuli and exit, one CTA per SM at a
+  // time for this kernel's shared memory)
+  const long long nblk = a.gen_list ? a.gen_n : NN / 8;
+  if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(adi_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adi_median_kernel<<<(unsigned)(NN / 8), 256, smem, st>>>(a, tcap);
+  adi_median_kernel<<<(unsigned)nblk, 256, smem, st>>>(a, tcap);
   return cudaGetLastError();
 }
 

@@ -655,7 +655,11 @@ struct GroupKey {
   }
 };
 std::mutex g_group_mu;
-std::map<GroupKey, std::pair<std::vector<int>, std::vector<int>>> g_group_cache;
+struct GroupLists {
+  std::vector<int> groups, class_off;
+  int gen_off, gen_n;
+};
+std::map<GroupKey, GroupLists> g_group_cache;
 
 }  // namespace
 
@@ -664,6 +668,8 @@ int plan_band_path(AdiPlanHost &ap, int64_t T, int32_t n) {
   ap.evq.clear();
   ap.groups.clear();
   ap.class_off.assign(NCLASS + 1, 0);
+  ap.gen_off = -1;
+  ap.gen_n = 0;
   if (ap.wmax == 0 || A <= 0) return GRAPHIC_OK;
   // event queries of every banded annulus: frame s is outside S_i for
   // a_s <= i < b_s (two pointers over the monotone gates)
@@ -685,13 +691,16 @@ int plan_band_path(AdiPlanHost &ap, int64_t T, int32_t n) {
     std::lock_guard<std::mutex> lk(g_group_mu);
     auto it = g_group_cache.find(key);
     if (it != g_group_cache.end()) {
-      ap.groups = it->second.first;
-      ap.class_off = it->second.second;
+      ap.groups = it->second.groups;
+      ap.class_off = it->second.class_off;
+      ap.gen_off = it->second.gen_off;
+      ap.gen_n = it->second.gen_n;
       return GRAPHIC_OK;
     }
   }
   const int64_t NN = (int64_t)n * n;
   std::vector<std::vector<int>> lists(NCLASS);
+  std::vector<int> gen_blocks;   // 8-pixel blocks of the general path
   for (int64_t g = 0; g < NN / PPC; g++) {
     int cls = 0;
     bool general = false;
@@ -711,15 +720,19 @@ int plan_band_path(AdiPlanHost &ap, int64_t T, int32_t n) {
       else cls = std::max(cls, class_of_width(W));
     }
     if (!general) lists[cls].push_back((int)g);
+    else if (gen_blocks.empty() || gen_blocks.back() != (int)(g / 2)) gen_blocks.push_back((int)(g / 2));
   }
   for (int k = 0; k < NCLASS; k++) {
     ap.class_off[k] = (int)ap.groups.size();
     ap.groups.insert(ap.groups.end(), lists[k].begin(), lists[k].end());
   }
   ap.class_off[NCLASS] = (int)ap.groups.size();
+  ap.gen_off = (int)ap.groups.size();
+  ap.gen_n = (int)gen_blocks.size();
+  ap.groups.insert(ap.groups.end(), gen_blocks.begin(), gen_blocks.end());
   std::lock_guard<std::mutex> lk(g_group_mu);
   if (g_group_cache.size() > 16) g_group_cache.clear();
-  g_group_cache[key] = {ap.groups, ap.class_off};
+  g_group_cache[key] = {ap.groups, ap.class_off, ap.gen_off, ap.gen_n};
   return GRAPHIC_OK;
 }
 

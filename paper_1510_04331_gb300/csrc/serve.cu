@@ -440,6 +440,9 @@ void issue_iteration(graphic_server *s) {
     a.evq = reinterpret_cast<const uint32_t *>(plan + r->o_evq);
     a.groups = reinterpret_cast<const int *>(plan + r->o_groups);
     for (int k = 0; k < 8; k++) a.class_off[k] = k < (int)r->ap.class_off.size() ? r->ap.class_off[k] : 0;
+    a.gen_list = r->ap.gen_off >= 0 ? 1 : 0;
+    a.gen_off = r->ap.gen_off;
+    a.gen_n = r->ap.gen_n;
     a.band_scratch = s->d_band;   // shared: the median launches run one after the other on s_comp
     a.band_scratch_cap = graphic::kBandScratchMax;
     a.status = s->d_status + r->slot;

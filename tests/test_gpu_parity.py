@@ -182,6 +182,57 @@ def test_collapse_bit_exact(g, T):
     assert np.array_equal(out.ravel()[pix], oracle.collapse_median(c, pixels=pix))
 
 
+@pytest.mark.parametrize("T", [40, 500])
+def test_adi_subtract_unsampled_spread_bit_exact(g, T):
+    """Median PSF pixels whose spread an even 32-frame sample (in angle
+    order) does not show: a constant sample around varying frames, heavy
+    outliers, half the sample far below the rest."""
+    n = 64
+    rng = np.random.default_rng(200 + T)
+    c = (rng.standard_normal((T, n, n)) * 50 + 100).astype(np.float32)   # angle order
+    pa = np.sort(rng.uniform(-40, 40, T))
+    sampled = (np.arange(32) * T) // 32
+    rest = np.setdiff1d(np.arange(T), sampled)
+    c[sampled, 10, :] = 7.0
+    out_i = rng.choice(T, T // 10, replace=False)
+    c[out_i, 11, :] = np.where(rng.random((out_i.size, 1)) < 0.5, -1e30, 1e30).astype(np.float32)
+    c[sampled[::2], 12, :] = -1e4
+    c[rest, 13, :] = np.float32(3.0)
+    perm = rng.permutation(T)
+    c, pa = c[perm].copy(), pa[perm].copy()
+    edges = [2.0, 9.0, 16.0, 30.0]
+    out = g.graphic_adi_subtract(dev(c), pa, 4.0, 1.5, edges).cpu().numpy()
+    pix = np.concatenate([np.arange(10 * n, 14 * n), rng.choice(n * n, 64, replace=False)])
+    ref = oracle.adi_subtract(c, pa, 4.0, 1.5, edges, pixels=pix)
+    assert np.array_equal(out.reshape(T, n * n)[:, pix].T, ref)
+
+
+@pytest.mark.parametrize("T", [32, 33, 64, 65, 500, 2000])
+def test_collapse_outliers_and_unsampled_spread_bit_exact(g, T):
+    """Pixels whose spread an even 32-frame sample of the cube does not show:
+    heavy outliers, a constant sample around varying frames, a median
+    outside the sample's range, a median equal to the sample's extreme."""
+    n = 64
+    rng = np.random.default_rng(100 + T)
+    c = (rng.standard_normal((T, n, n)) * 10).astype(np.float32)
+    sampled = (np.arange(32) * T) // 32
+    rest = np.setdiff1d(np.arange(T), sampled)
+    out_i = rng.choice(T, T // 10, replace=False)
+    c[out_i, 0, 0] = np.where(rng.random(out_i.size) < 0.5, -1e30, 1e30).astype(np.float32)
+    c[:, 0, 1] = 5.0
+    c[rest, 0, 1] = rng.standard_normal(rest.size).astype(np.float32)
+    c[sampled, 0, 2] = 0.0
+    c[rest, 0, 2] = np.arange(1, rest.size + 1, dtype=np.float32)
+    c[:, 0, 3] = np.float32(2.0)
+    c[sampled[: 16], 0, 3] = np.float32(-7.0)
+    c[rest, 0, 3] = rng.uniform(-7, 30, rest.size).astype(np.float32)
+    c[:, 0, 4] = np.float32(-7.0)
+    k = min(rest.size, T // 2 + 2)
+    c[rest[:k], 0, 4] = rng.uniform(0, 1, k).astype(np.float32)
+    out = g.graphic_collapse_median(dev(c)).cpu().numpy()
+    assert np.array_equal(out, np.median(c, axis=0).astype(np.float32))
+
+
 # --------------------------------------------------------------------------
 # whole reduction
 # --------------------------------------------------------------------------
