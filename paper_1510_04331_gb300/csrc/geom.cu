@@ -676,11 +676,20 @@ __global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) li
   constexpr int HP = PPC / 2;                      // 16-byte pieces per row of the CTA's columns
   const int col0 = 2 * PPC * blockIdx.x;           // first column of the CTA
   if constexpr (COLS) {
-    for (int i = threadIdx.x; i < HP * NIN; i += 32 * PPC) {
-      const int row = i / HP, h = i % HP;
-      const float4 q4 = *reinterpret_cast<const float4 *>(fin + (size_t)row * RS + col0 + 4 * h);
-      sbuf[2 * h][pad32(row)] = make_float2(q4.x, q4.y);
-      sbuf[2 * h + 1][pad32(row)] = make_float2(q4.z, q4.w);
+    // every piece's load is issued before the first shared-memory store
+    constexpr int IT = HP * NIN / (32 * PPC);
+    static_assert(IT * 32 * PPC == HP * NIN, "pieces per thread");
+    float4 q4[IT];
+#pragma unroll
+    for (int k = 0; k < IT; k++) {
+      const int i = threadIdx.x + k * 32 * PPC, row = i / HP, h = i % HP;
+      q4[k] = *reinterpret_cast<const float4 *>(fin + (size_t)row * RS + col0 + 4 * h);
+    }
+#pragma unroll
+    for (int k = 0; k < IT; k++) {
+      const int i = threadIdx.x + k * 32 * PPC, row = i / HP, h = i % HP;
+      sbuf[2 * h][pad32(row)] = make_float2(q4[k].x, q4[k].y);
+      sbuf[2 * h + 1][pad32(row)] = make_float2(q4[k].z, q4[k].w);
     }
     __syncthreads();
   }
@@ -692,25 +701,41 @@ __global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) li
   const bool RCOLS = (KIND == ROT_P1) && (q & 1);
   if (RCOLS) {
     if (q == 1) {
-      for (int i = threadIdx.x; i < 2 * N; i += 32 * PPC) {
-        const int row = i >> 1, h = i & 1;
-        if (row == 0) continue;                        // would be element n
-        const float4 q4 = *reinterpret_cast<const float4 *>(fin + (size_t)row * N + col0 + 4 * h);
-        sbuf[2 * h][pad32(N - row)] = make_float2(q4.x, q4.y);
-        sbuf[2 * h + 1][pad32(N - row)] = make_float2(q4.z, q4.w);
+      constexpr int IT = 2 * N / (32 * PPC);
+      float4 q4[IT];
+#pragma unroll
+      for (int k = 0; k < IT; k++) {
+        const int i = threadIdx.x + k * 32 * PPC, row = i >> 1, h = i & 1;
+        q4[k] = row == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)   // row 0 would be element n
+                         : *reinterpret_cast<const float4 *>(fin + (size_t)row * N + col0 + 4 * h);
+      }
+#pragma unroll
+      for (int k = 0; k < IT; k++) {
+        const int i = threadIdx.x + k * 32 * PPC, row = i >> 1, h = i & 1;
+        if (row == 0) continue;
+        sbuf[2 * h][pad32(N - row)] = make_float2(q4[k].x, q4[k].y);
+        sbuf[2 * h + 1][pad32(N - row)] = make_float2(q4[k].z, q4[k].w);
       }
       if (threadIdx.x < PPC) sbuf[threadIdx.x][pad32(0)] = make_float2(0.f, 0.f);
     } else {
       const int cb = N - col0 - 8;                     // >= 0, multiple of 8
-      for (int pos = threadIdx.x; pos < N; pos += 32 * PPC) {
-        const float *rowp = fin + (size_t)pos * N;
-        const float4 lo4 = *reinterpret_cast<const float4 *>(rowp + cb);
-        const float4 hi4 = *reinterpret_cast<const float4 *>(rowp + cb + 4);
-        const float top = (col0 > 0) ? rowp[N - col0] : 0.f;   // line 0 of the frame is zero
-        sbuf[0][pad32(pos)] = make_float2(top, hi4.w);
-        sbuf[1][pad32(pos)] = make_float2(hi4.z, hi4.y);
-        sbuf[2][pad32(pos)] = make_float2(hi4.x, lo4.w);
-        sbuf[3][pad32(pos)] = make_float2(lo4.z, lo4.y);
+      constexpr int IT = N / (32 * PPC);
+      float4 lo4[IT], hi4[IT];
+      float top[IT];
+#pragma unroll
+      for (int k = 0; k < IT; k++) {
+        const float *rowp = fin + (size_t)(threadIdx.x + k * 32 * PPC) * N;
+        lo4[k] = *reinterpret_cast<const float4 *>(rowp + cb);
+        hi4[k] = *reinterpret_cast<const float4 *>(rowp + cb + 4);
+        top[k] = (col0 > 0) ? rowp[N - col0] : 0.f;   // line 0 of the frame is zero
+      }
+#pragma unroll
+      for (int k = 0; k < IT; k++) {
+        const int pos = threadIdx.x + k * 32 * PPC;
+        sbuf[0][pad32(pos)] = make_float2(top[k], hi4[k].w);
+        sbuf[1][pad32(pos)] = make_float2(hi4[k].z, hi4[k].y);
+        sbuf[2][pad32(pos)] = make_float2(hi4[k].x, lo4[k].w);
+        sbuf[3][pad32(pos)] = make_float2(lo4[k].z, lo4[k].y);
       }
     }
     __syncthreads();
