@@ -201,11 +201,17 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
   // from here on every warp works alone, on its own pixel's column
   const int ann = ann_s[w];
   uint32_t *kcol = keys + w;   // key of frame s: kcol[s * KS]
+  // keys in place, with the finiteness check and the extremes
   bool bad = false;
+  uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll 4
   for (int s = lane; s < T; s += 32) {
     const float v = __uint_as_float(kcol[s * KS]);
     bad |= !isfinite(v);
-    kcol[s * KS] = f2key(v);
+    const uint32_t k = f2key(v);
+    kcol[s * KS] = k;
+    kmin = min(kmin, k);
+    kmax = max(kmax, k);
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
   __syncwarp();
@@ -219,14 +225,12 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
   const int nbd = bhi - blo + 1;
   const uint32_t *kw = kcol;
   const unsigned lt = (1u << lane) - 1u;
+  // each candidate's event queries are gathered asynchronously into this
+  // warp's key column as the candidate is found (entry j at kcol[j * KS]:
+  // j never passes the frame being read, whose key is already in registers)
+  const uint32_t *evq = B.evq + (size_t)ann * T;
 
   // ---- extremes ----------------------------------------------------------
-  uint32_t kmin = 0xffffffffu, kmax = 0u;
-  for (int s = lane; s < T; s += 32) {
-    const uint32_t k = kw[s * KS];
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
-  }
   kmin = __reduce_min_sync(FULL, kmin);
   kmax = __reduce_max_sync(FULL, kmax);
 
@@ -271,6 +275,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
           const int j = nc + __popc(mc & lt);
           ckey[j] = k[u];
           cs[j] = (uint16_t)s;
+          cp_async4(&kcol[j * KS], evq + s);
           cmin = min(cmin, k[u]);
           cmax = max(cmax, k[u]);
         }
@@ -313,6 +318,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
         if (j < B.cap) {
           ckey[j] = k;
           cs[j] = (uint16_t)s;
+          cp_async4(&kcol[j * KS], evq + s);
         }
         cmin = min(cmin, k);
         cmax = max(cmax, k);
@@ -324,6 +330,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
   }
   cmin = __reduce_min_sync(FULL, cmin);
   cmax = __reduce_max_sync(FULL, cmax);
+  cp_async_wait_all();
   __syncwarp();
   bool ok = nc <= B.cap && nc >= nbd;
 
@@ -347,7 +354,6 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
     uint32_t *skeys_g = reinterpret_cast<uint32_t *>(slot + L.skeys);
     uint32_t *blev_g = reinterpret_cast<uint32_t *>(slot + L.blev);
     uint16_t *blpos_g = reinterpret_cast<uint16_t *>(slot + L.blpos);
-    const uint32_t *evq = B.evq + (size_t)ann * T;
     const int off = nbelow - blo;   // value position = off + rank among the candidates
     for (int j0 = 0; j0 < nc; j0 += 32) {
       const int j = j0 + lane;
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
       if (inb) {
         const int jj = nbb + __popc(mi & lt);
         blpos_g[jj] = (uint16_t)pos;
-        blev_g[jj] = __ldg(&evq[s]);
+        blev_g[jj] = kcol[j * KS];
       }
       nbb += __popc(mi);
     }
@@ -437,14 +443,18 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   const int nb = hdr.x, nbelow = hdr.y, ann = hdr.z;
   bool act = ann >= 0 && hdr.w == 1 && nb <= NB;
   if (act) {
-    const uint32_t *sk = reinterpret_cast<const uint32_t *>(slot + SL.skeys);
-    const uint32_t *bl = reinterpret_cast<const uint32_t *>(slot + SL.blev);
-    const uint16_t *bp = reinterpret_cast<const uint16_t *>(slot + SL.blpos);
-    for (int j = lane; j < nb; j += 32) {
-      skeys[j] = sk[j];
-      blev[j] = bl[j];
-      blpos[j] = bp[j];
+    // band keys, event queries and value positions: 16-byte asynchronous
+    // copies (the arrays start on 16-byte boundaries in the slot and here;
+    // whole pieces stay within the capacity NB)
+    const int nk = (nb + 3) >> 2, np = (nb + 7) >> 3;
+    for (int q = lane; q < 2 * nk + np; q += 32) {
+      if (q < nk) cp_async16(skeys + 4 * q, slot + SL.skeys + 16 * q);
+      else if (q < 2 * nk) cp_async16(blev + 4 * (q - nk), slot + SL.blev + 16 * (q - nk));
+      else cp_async16(blpos + 8 * (q - 2 * nk), slot + SL.blpos + 16 * (q - 2 * nk));
     }
+  }
+  cp_async_commit();
+  if (act) {
     // BELOW words and the BELOW frames before each (exclusive prefix)
     const uint32_t *bw = reinterpret_cast<const uint32_t *>(slot + SL.below);
     uint32_t carry = 0;
@@ -485,6 +495,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   // band position p (value order) is a member at query c C unless its frame's
   // exclusion queries [a, b) hold c C, i.e. unless ceil(a/C) <= c < ceil(b/C):
   // one 32-bit chunk mask per position, transposed into the lanes' words
+  cp_async_wait_group<1>();   // the band data (the first value block may still be in flight)
+  __syncwarp();
   if (act) {
     for (int j = lane; j < nb; j += 32) bm[blpos[j]] = blev[j];   // event queries by value position
     __syncwarp();
@@ -529,6 +541,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   bool lane_ok = act && i0 < T;
   int wi = 0, base = 0;   // word of the current member, members in the words below it
   bool fail = false;
+  // the gate of the lane's next query is loaded one query ahead
+  int2 gnext = lane_ok ? __ldg(&gate_g[i0]) : make_int2(0, 0);
 
   // ---- sweep ------------------------------------------------------------
   for (int b = 0; b < nblk; b++) {
@@ -545,6 +559,8 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
       if (b * SWK + kk >= C || i >= i1) break;
       float res = 0.0f;
       if (lane_ok) {
+        const int2 gv = gnext;
+        if (i + 1 < i1) gnext = __ldg(&gate_g[i + 1]);
         // events of query i, leaving (a == i) and entering (b == i) members
         // from one merged stream
         while (ne == i) {
@@ -563,7 +579,6 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
           }
           ne = min(na, nq);
         }
-        const int2 gv = __ldg(&gate_g[i]);
         const int Li = gv.x, Ri = gv.y;
         // BELOW members of S_i: BELOW frames before L_i and from R_i on
         const uint2 ul = belowc[Li >> 5], ur = belowc[Ri >> 5];
