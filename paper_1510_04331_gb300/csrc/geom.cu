@@ -499,9 +499,22 @@ __device__ __forceinline__ void w32_row(float2 (&a)[32]) {
   a[8 * K1 + 7] = mul_w32<7 * K1>(a[8 * K1 + 7]);
 }
 
+// HALF: a[16..31] are zero (a line zero-padded to twice its length), so
+// each inner DFT4 has two inputs.
+template <bool HALF = false>
 __device__ __forceinline__ void dft32(float2 (&a)[32]) {
 #pragma unroll
-  for (int n2 = 0; n2 < 8; n2++) dft4(a[n2], a[n2 + 8], a[n2 + 16], a[n2 + 24]);
+  for (int n2 = 0; n2 < 8; n2++) {
+    if constexpr (HALF) {
+      const float2 x0 = a[n2], x1 = a[n2 + 8];
+      a[n2] = cadd(x0, x1);
+      a[n2 + 8] = make_float2(x0.x + x1.y, x0.y - x1.x);    // x0 - i x1
+      a[n2 + 16] = csub(x0, x1);
+      a[n2 + 24] = make_float2(x0.x - x1.y, x0.y + x1.x);   // x0 + i x1
+    } else {
+      dft4(a[n2], a[n2 + 8], a[n2 + 16], a[n2 + 24]);
+    }
+  }
   w32_row<1>(a);
   w32_row<2>(a);
   w32_row<3>(a);
@@ -524,9 +537,10 @@ __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 // Two radix-32 Stockham stages over the 1024-point line held as v[m] =
 // element lane + 32 m: after the call v[r] = X[lane + 32 r].  buf: the warp's
 // exchange buffer (1024 + 32 entries); tw: W_1024^(r lane) at [r][lane].
+template <bool HALF = false>
 __device__ __forceinline__ void fft1024_warp(float2 (&v)[32], int lane, float2 *buf,
                                              const float2 *__restrict__ tw) {
-  dft32(v);
+  dft32<HALF>(v);
 #pragma unroll
   for (int r = 0; r < 32; r++) buf[pad32(32 * lane + r)] = v[r];
   __syncwarp();
@@ -548,7 +562,7 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
                                            const LineParam &la, const LineParam &lb) {
   constexpr int M = 1024;
   constexpr bool SAME_D = (KIND == SHIFT_X || KIND == SHIFT_Y);
-  fft1024_warp(v, lane, buf, tw);
+  fft1024_warp<KIND != ROT_P3>(v, lane, buf, tw);   // only rotation pass 3 reads whole 1024-point lines
 
   // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
   if constexpr (!SAME_D) {
