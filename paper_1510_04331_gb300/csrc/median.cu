@@ -55,6 +55,10 @@ __device__ __forceinline__ int annulus_of(long long p, int n, const double *edge
 // reductions.
 constexpr int COL_PPC = 4;
 constexpr int COL_KS = 5;
+// collapse2_kernel: words per frame row (one 16-byte copy per frame; a
+// warp's column reads meet 4-way bank conflicts, cheaper here than four
+// 4-byte copies per frame)
+constexpr int C2_KS = 4;
 
 // MASKED (master sky, Sect. 3.2): values that are not finite or fall in the
 // frame's star mask are left out -- they get the largest key, so they rank
@@ -222,31 +226,30 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
 }
 
 // Median collapse of unmasked cubes that fit shared memory.  Per pixel
-// (one warp): the values in shared memory (odd row stride, conflict-free).
+// (one warp): the values in shared memory, one 16-byte row of the CTA's 4
+// pixels per frame.
 // A 256-bin histogram linear in value over the interquartile range of 32
 // sampled frames (values outside it counted below or ignored above), filled
 // in one pass over the raw values, locates the bins of the two middle
 // ranks; a second pass copies the total-order keys of those bins (a few
-// values) into the row padding words, and the middle ranks are read off by
-// counting within that list.  A middle rank outside the range, a list
-// longer than its capacity (many equal values) or a non-finite value falls
-// back to exact radix selects of the two middle ranks over all keys.
+// values) into the warp's second 256 histogram words, and the middle ranks
+// are read off by counting within that list.  A middle rank outside the
+// range, a list longer than 256 keys (many equal values) or a non-finite
+// value falls back to exact radix selects of the two middle ranks over all
+// keys.
 __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
   uint32_t *hist_all = csm;                       // [COL_PPC][512]
-  uint32_t *keys_all = csm + COL_PPC * 512;       // [T][COL_KS]
+  uint32_t *keys_all = csm + COL_PPC * 512;       // [T][C2_KS]
   const int T = (int)a.T;
   const long long NN = a.fs ? a.fs : (long long)a.n * a.n;   // frame stride
   const long long p0 = (long long)blockIdx.x * COL_PPC;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = threadIdx.x; j < COL_PPC * T; j += 32 * COL_PPC) {
-    const int t = j >> 2, q = j & 3;
-    cp_async4(keys_all + t * COL_KS + q, a.in + (long long)t * NN + p0 + q);
-  }
+  for (int t = threadIdx.x; t < T; t += 32 * COL_PPC) cp_async16(keys_all + t * C2_KS, a.in + (long long)t * NN + p0);
   cp_async_wait_all();
   __syncthreads();
   uint32_t *hist = hist_all + w * 512;
-  uint32_t *kw = keys_all + w;   // value (then key) of frame t: kw[t * COL_KS]
+  uint32_t *kw = keys_all + w;   // value (then key) of frame t: kw[t * C2_KS]
   const uint32_t k0 = (uint32_t)((T - 1) / 2);
   const bool even = (T & 1) == 0;
   const uint32_t k1 = even ? k0 + 1 : k0;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
   // for a range the sample missed, the exact path below takes over.
   float lo = 0.f, scale = 0.f;
   if (T >= 32) {
-    float x = __uint_as_float(kw[(int)(((long long)lane * T) >> 5) * COL_KS]);
+    float x = __uint_as_float(kw[(int)(((long long)lane * T) >> 5) * C2_KS]);
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
   uint32_t nb = 0;
 #pragma unroll 4
   for (int t = lane; t < T; t += 32) {
-    const float v = __uint_as_float(kw[t * COL_KS]);
+    const float v = __uint_as_float(kw[t * C2_KS]);
     bad |= !isfinite(v);
     const float xv = (v - lo) * scale;
     if (xv < 0.f) nb++;
@@ -344,11 +347,11 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     }
   }
   const int nlist = in_range ? (int)(bel[1] + hist[bin[1]] - bel[0]) : 0x7fffffff;
-  // the list lives in the padding word of rows [w cap, (w + 1) cap)
-  const int cap = min(T / COL_PPC, 256);
+  // the list lives in the warp's second 256 histogram words
+  const int cap = min(T, 256);
   float med;
   if (!anybad && nlist <= cap) {
-    uint32_t *cbuf = keys_all + (size_t)w * cap * COL_KS + (COL_KS - 1);   // element j at cbuf[j * COL_KS]
+    uint32_t *cbuf = hist + 256;   // element j at cbuf[j] (the second histogram's words)
     const unsigned lt = (1u << lane) - 1u;
     int len = 0;
     // four 32-frame rounds per step: their loads and bins are independent;
@@ -359,14 +362,14 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int t = t0 + 32 * u + lane;
-        v[u] = t < T ? __uint_as_float(kw[t * COL_KS]) : 0.f;
+        v[u] = t < T ? __uint_as_float(kw[t * C2_KS]) : 0.f;
         const float xv = (v[u] - lo) * scale;
         in[u] = t < T && xv >= 0.f && xv < 256.f && (unsigned)((int)xv - bin[0]) <= (unsigned)(bin[1] - bin[0]);
       }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const unsigned mm = __ballot_sync(FULL, in[u]);
-        if (in[u]) cbuf[(len + __popc(mm & lt)) * COL_KS] = f2key(v[u]);
+        if (in[u]) cbuf[len + __popc(mm & lt)] = f2key(v[u]);
         len += __popc(mm);
       }
     }
@@ -375,10 +378,10 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     const uint32_t r0 = k0 - bel[0], r1 = k1 - bel[0];
     uint32_t f0 = 0xffffffffu, f1 = 0xffffffffu;
     for (int j = lane; j < len; j += 32) {
-      const uint32_t kj = cbuf[j * COL_KS];
+      const uint32_t kj = cbuf[j];
       uint32_t nlt = 0, nle = 0;
       for (int x = 0; x < len; x++) {
-        const uint32_t kx = cbuf[x * COL_KS];
+        const uint32_t kx = cbuf[x];
         nlt += kx < kj ? 1u : 0u;
         nle += kx <= kj ? 1u : 0u;
       }
@@ -392,8 +395,8 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     // exact: keys in place, then radix selects of the two middle ranks
     uint32_t orv = 0u, andv = 0xffffffffu;
     for (int t = lane; t < T; t += 32) {
-      const uint32_t k = f2key(__uint_as_float(kw[t * COL_KS]));
-      kw[t * COL_KS] = k;
+      const uint32_t k = f2key(__uint_as_float(kw[t * C2_KS]));
+      kw[t * C2_KS] = k;
       orv |= k;
       andv &= k;
     }
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     andv = __reduce_and_sync(FULL, andv);
     __syncwarp();
     uint32_t Klo, Khi, clo, chi;
-    band_select2<COL_KS>(kw, T, k0, k1, orv ^ andv, andv, hist, hist + 256, lane, Klo, clo, Khi, chi);
+    band_select2<C2_KS>(kw, T, k0, k1, orv ^ andv, andv, hist, hist + 256, lane, Klo, clo, Khi, chi);
     med = even ? (key2f(Klo) + key2f(Khi)) * 0.5f : key2f(Klo);
   }
   if (lane == 0) a.out[p0 + w] = med;
@@ -703,11 +706,18 @@ cudaError_t launch_adi_general(const AdiArgs &a, cudaStream_t st, int tcap);
 cudaError_t launch_collapse(const CollapseArgs &a, cudaStream_t st) {
   const long long NN = (long long)a.n * a.n;
   const unsigned grid = (unsigned)(NN / COL_PPC);
-  if (a.T <= 8192) {
-    const size_t smem = (size_t)(COL_PPC * 512 + COL_KS * a.T) * sizeof(uint32_t);
+  const long long fs = a.fs ? a.fs : NN;
+  const bool rows16 = ((uintptr_t)a.in & 15) == 0 && (fs & 3) == 0;   // 16-byte frame rows of 4 pixels
+  if (a.T <= 8192 && rows16) {
+    const size_t smem = (size_t)(COL_PPC * 512 + C2_KS * a.T) * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(collapse2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     collapse2_kernel<<<grid, 32 * COL_PPC, smem, st>>>(a);
+  } else if (a.T <= 8192) {
+    const size_t smem = (size_t)(COL_PPC * 256 + COL_KS * a.T) * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(collapse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    collapse_kernel<true><<<grid, 32 * COL_PPC, smem, st>>>(a);
   } else {
     const size_t smem = (size_t)(COL_PPC * 256) * sizeof(uint32_t);
     collapse_kernel<false><<<grid, 32 * COL_PPC, smem, st>>>(a);
