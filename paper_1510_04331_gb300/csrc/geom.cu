@@ -755,27 +755,55 @@ __global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) li
     __syncthreads();
   }
   float2 v[32];
+  if constexpr (KIND == ROT_P1) {
+    // one branch per line pair, not per element, so that each form's loads
+    // are issued together: staged columns (odd quarter turns), rows (q = 0)
+    // or rows read backwards (q = 2: element pos >= 1 of line i >= 1 is
+    // frame[n - i][n - pos])
+    if (RCOLS) {
 #pragma unroll
-  for (int m = 0; m < 32; m++) {
-    const int pos = lane + 32 * m;
-    float2 z = make_float2(0.f, 0.f);
-    if (32 * m < NIN) {
-      if (COLS || RCOLS) {
-        z = buf[pad32(pos)];
-      } else if constexpr (KIND == SHIFT_X) {
-        z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
-      } else if constexpr (KIND == SHIFT_Y) {
-        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
-      } else if constexpr (KIND == ROT_P1) {
-        z = load_rot90_pair(fin, N, q, line0, pos);
-      } else if constexpr (KIND == ROT_P2) {
-        z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
-      } else {
-        z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+      for (int m = 0; m < 32; m++) v[m] = (32 * m < NIN) ? buf[pad32(lane + 32 * m)] : make_float2(0.f, 0.f);
+    } else if (q == 0) {
+#pragma unroll
+      for (int m = 0; m < 32; m++) {
+        const int pos = lane + 32 * m;
+        v[m] = (32 * m < NIN) ? make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos])
+                              : make_float2(0.f, 0.f);
       }
-      if constexpr (KIND == SHIFT_X || KIND == ROT_P1) bad |= !finite_pair(z);
+    } else {
+      const float *r0 = fin + (size_t)(N - line0) * N + N;        // row n - line0 (unused for line0 = 0), + n
+      const float *r1 = fin + (size_t)(N - line0 - 1) * N + N;    // row n - line0 - 1, + n
+#pragma unroll
+      for (int m = 0; m < 32; m++) {
+        const int pos = lane + 32 * m;
+        float2 z = make_float2(0.f, 0.f);
+        if (32 * m < NIN && pos >= 1) z = make_float2(line0 >= 1 ? r0[-pos] : 0.f, r1[-pos]);
+        v[m] = z;
+      }
     }
-    v[m] = z;
+#pragma unroll
+    for (int m = 0; m < 32; m++) bad |= !finite_pair(v[m]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < 32; m++) {
+      const int pos = lane + 32 * m;
+      float2 z = make_float2(0.f, 0.f);
+      if (32 * m < NIN) {
+        if (COLS) {
+          z = buf[pad32(pos)];
+        } else if constexpr (KIND == SHIFT_X) {
+          z = make_float2(fin[(size_t)line0 * N + pos], fin[(size_t)(line0 + 1) * N + pos]);
+        } else if constexpr (KIND == SHIFT_Y) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * N + line0);
+        } else if constexpr (KIND == ROT_P2) {
+          z = *reinterpret_cast<const float2 *>(fin + (size_t)pos * M + line0);
+        } else {
+          z = make_float2(fin[(size_t)line0 * M + pos], fin[(size_t)(line0 + 1) * M + pos]);
+        }
+        if constexpr (KIND == SHIFT_X) bad |= !finite_pair(z);
+      }
+      v[m] = z;
+    }
   }
   if constexpr (KIND == SHIFT_X || KIND == ROT_P1) {
     if (bad) atomicOr(a.status, STATUS_NONFINITE);
