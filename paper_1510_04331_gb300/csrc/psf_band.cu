@@ -27,7 +27,7 @@
 //     counting) ranks the candidates.  When the located bins hold more than
 //     the candidate capacity (heavy outliers, many ties) an exact radix
 //     select of the keys of ranks blo and bhi and a tie-aware extraction
-//     give the band directly.  Writes per pixel: the band's keys in value
+//     give the band directly.  Writes per pixel: the band's values in value
 //     order, the band's members in frame order (value position, event
 //     queries) and the BELOW bit map over s.
 //   band_sweep_kernel  lane c sweeps the queries [cC, cC + C), C = ceil(T/32):
@@ -66,7 +66,7 @@ __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~(size_t
 // Per-pixel slot written by band_prep_kernel and read by band_sweep_kernel,
 // for band capacity NB and nwt = ceil(T / 32) BELOW words.
 //   header   int4 (band size nb, BELOW count, annulus or -1, 1 = ok)
-//   skeys    [NB] u32   band keys in value order
+//   skeys    [NB] u32   band values (float bits) in value order
 //   blev     [NB] u32   band members in frame order: event queries a | b << 16
 //   blpos    [NB] u16   band members in frame order: value position
 //   below    [nwt] u32  bit s: frame s is below the band
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
           atomicOr(&below[s >> 5], 1u << (s & 31));
           nfix++;
         } else if (pos < nbd) {
-          skeys_g[pos] = k;
+          skeys_g[pos] = __float_as_uint(key2f(k));   // the sweep reads values
           inb = true;
         }
       }
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   const int nb = hdr.x, nbelow = hdr.y, ann = hdr.z;
   bool act = ann >= 0 && hdr.w == 1 && nb <= NB;
   if (act) {
-    // band keys, event queries and value positions: 16-byte asynchronous
+    // band values, event queries and value positions: 16-byte asynchronous
     // copies (the arrays start on 16-byte boundaries in the slot and here;
     // whole pieces stay within the capacity NB)
     const int nk = (nb + 3) >> 2, np = (nb + 7) >> 3;
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
         }
         if (t >= base && t < base + pc) {
           const int pos = nth_set(wd, t - base);
-          float med = key2f(skeys[wi * 32 + pos]);
+          float med = __uint_as_float(skeys[wi * 32 + pos]);
           // the next member, needed for an even |S_i| (found for every lane:
           // the lanes' parities differ, so a branch would run both ways):
           // a higher bit of this word, else the first of a later word
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
             rest = bm[wn * 32 + c];
           }
           const bool even = (nset & 1) == 0;
-          const float hi = key2f(skeys[rest ? wn * 32 + __ffs(rest) - 1 : wi * 32 + pos]);
+          const float hi = __uint_as_float(skeys[rest ? wn * 32 + __ffs(rest) - 1 : wi * 32 + pos]);
           if (even) {
             if (rest) med = (med + hi) * 0.5f;
             else fail = true;
