@@ -570,7 +570,9 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
     for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
     __syncwarp();
   }
-  const float inv_m = 1.0f / (float)M;
+  // the 1/m of the inverse and the 1/2 of the pair separation are powers of
+  // two, carried by the phasors (the same bits as scaling each product)
+  constexpr float sc = SAME_D ? 1.0f / (float)M : 0.5f / (float)M;
   // phasors H_k = exp(-i 2 pi ks delta), ks the signed bin: exact anchors at
   // r = 0, 8, 16, 24, a product with exp(-i 2 pi 32 delta) in between
   const float2 sa = phase_at(la, 32);
@@ -581,29 +583,36 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
     const int k = lane + 32 * r;
     if ((r & 7) == 0) {
       const int ks = (r < 16) ? k : k - M;
-      ha = phase_at(la, ks);
-      hb = SAME_D ? ha : phase_at(lb, ks);
+      const float2 pa = phase_at(la, ks);
+      ha = make_float2(pa.x * sc, pa.y * sc);
+      if constexpr (SAME_D) {
+        hb = ha;
+      } else {
+        const float2 pb = phase_at(lb, ks);
+        hb = make_float2(pb.x * sc, pb.y * sc);
+      }
     } else {
       ha = cmul(ha, sa);
       hb = SAME_D ? ha : cmul(hb, sb);
     }
     float2 ua = ha, ub = hb;
     if (r == 16 && lane == 0) {   // Nyquist bin
-      ua = make_float2(la.cnyq, 0.f);
-      ub = make_float2(lb.cnyq, 0.f);
+      ua = make_float2(la.cnyq * sc, 0.f);
+      ub = make_float2(lb.cnyq * sc, 0.f);
     }
     const float2 z = v[r];
     float2 vk;
     if constexpr (SAME_D) {
       vk = cmul(z, ua);
     } else {
+      // twice the spectra of lines a and b
       const float2 zm = buf[pad32((M - k) & (M - 1))];
-      const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+      const float2 A = make_float2(z.x + zm.x, z.y - zm.y);
+      const float2 B = make_float2(z.y + zm.y, zm.x - z.x);
       const float2 P = cmul(A, ua), Q = cmul(B, ub);
       vk = make_float2(P.x - Q.y, P.y + Q.x);
     }
-    v[r] = make_float2(vk.x * inv_m, -vk.y * inv_m);   // conj(V) / m
+    v[r] = make_float2(vk.x, -vk.y);   // conj(V) / m
   }
   __syncwarp();
 
