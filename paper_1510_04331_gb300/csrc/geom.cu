@@ -620,12 +620,13 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
   fft1024_warp(v, lane, buf, tw);
 }
 
-// Line pairs (warps) per CTA: 4 (column passes move 32-byte row pieces of
-// their 8 adjacent columns; 8 pairs per CTA with 64-byte pieces measured
-// slower: shift columns 2.46 -> 2.70 ms per survey step).  Register budget
-// for 16 resident warps per SM (measured faster than 12 for every kind).
+// Line pairs (warps) per CTA: 8 for rotation pass 2 (64-byte row pieces of
+// its 16 adjacent scratch columns: 5.05 -> 4.91 ms per survey step; 16
+// pairs 6.23 ms), 4 for the others (shift columns with 8 pairs: 1.88 ->
+// 2.17 ms).  Register budget for 16 resident warps per SM (measured faster
+// than 12 for every kind).
 template <int KIND>
-constexpr int w32_ppc() { return 4; }
+constexpr int w32_ppc() { return KIND == ROT_P2 ? 8 : 4; }
 constexpr size_t w32_smem_bytes(int ppc) { return (size_t)ppc * (1024 + 1024 / 32) * sizeof(float2); }
 
 template <int KIND>

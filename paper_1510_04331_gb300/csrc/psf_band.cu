@@ -189,30 +189,41 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
   __shared__ int ann_s[PPC];
 
   if (lane == 0) ann_s[w] = annulus_of(p0 + w, a.n, a.edge2, a.n_ann);
-  // the group's 4 pixels of every frame, angle order: one 16-byte copy each
-  if (a.perm_id) {
-    for (int s = threadIdx.x; s < T; s += 32 * PPC) cp_async16(keys + KS * s, a.in + (long long)s * a.in_fs + p0);
-  } else {
-    for (int s = threadIdx.x; s < T; s += 32 * PPC)
-      cp_async16(keys + KS * s, a.in + (long long)__ldg(&a.perm[s]) * a.in_fs + p0);
+  // the group's 4 pixels of every frame, angle order: one 16-byte copy each,
+  // in four quarters, so that the key conversion of a quarter overlaps the
+  // copies of the later ones
+  const int Q = ((T + 127) / 128) * 32;   // frames per quarter, a multiple of 32
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int s1 = min(T, (k + 1) * Q);
+    for (int s = k * Q + threadIdx.x; s < s1; s += 32 * PPC)
+      cp_async16(keys + KS * s, a.in + (long long)(a.perm_id ? s : __ldg(&a.perm[s])) * a.in_fs + p0);
+    cp_async_commit();
   }
-  cp_async_wait_all();
-  __syncthreads();
-  // from here on every warp works alone, on its own pixel's column
-  const int ann = ann_s[w];
   uint32_t *kcol = keys + w;   // key of frame s: kcol[s * KS]
-  // keys in place, with the finiteness check and the extremes
+  // keys in place, with the finiteness check and the extremes; each warp
+  // works on its own pixel's column
   bool bad = false;
   uint32_t kmin = 0xffffffffu, kmax = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k == 0) cp_async_wait_group<3>();
+    else if (k == 1) cp_async_wait_group<2>();
+    else if (k == 2) cp_async_wait_group<1>();
+    else cp_async_wait_group<0>();
+    __syncthreads();   // quarter k of every thread's copies has landed
+    const int s1 = min(T, (k + 1) * Q);
 #pragma unroll 4
-  for (int s = lane; s < T; s += 32) {
-    const float v = __uint_as_float(kcol[s * KS]);
-    bad |= !isfinite(v);
-    const uint32_t k = f2key(v);
-    kcol[s * KS] = k;
-    kmin = min(kmin, k);
-    kmax = max(kmax, k);
+    for (int s = k * Q + lane; s < s1; s += 32) {
+      const float v = __uint_as_float(kcol[s * KS]);
+      bad |= !isfinite(v);
+      const uint32_t key = f2key(v);
+      kcol[s * KS] = key;
+      kmin = min(kmin, key);
+      kmax = max(kmax, key);
+    }
   }
+  const int ann = ann_s[w];   // written before the barriers above
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.status, STATUS_NONFINITE);
   __syncwarp();
   char *slot = B.slots + ((size_t)blockIdx.x * PPC + w) * B.slot_bytes;

@@ -184,9 +184,13 @@ void CUDART_CB on_wake(void *p) {
 
 void CUDART_CB on_req_done(void *p) {
   Req *r = static_cast<Req *>(p);
+  // once gpu_done is set the scheduler may retire r and a waiter free it:
+  // read the server first and set the flag under the server mutex, which
+  // retiring needs, so that r is not touched after it may be gone
+  graphic_server *srv = r->srv;
+  std::lock_guard<std::mutex> lk(srv->mu);
   r->gpu_done.store(true);
-  std::lock_guard<std::mutex> lk(r->srv->mu);
-  r->srv->cv_sched.notify_all();
+  srv->cv_sched.notify_all();
 }
 
 int status_code(int bits) {
@@ -203,8 +207,10 @@ void fail_req(Req *r, int code, const std::string &msg) {
   }
 }
 
-// Free a finished request's resources and publish it.
+// Free a finished request's resources and publish it (a waiter may free r
+// right after; iterations still in flight stop referring to it first).
 void retire(graphic_server *s, Req *r) {
+  for (Iter &it : s->inflight) it.batch.erase(std::remove(it.batch.begin(), it.batch.end(), r), it.batch.end());
   if (r->off_cube != Arena::kNone) s->arena.release(r->off_cube, r->cube_bytes);
   if (r->off_out != Arena::kNone) s->arena.release(r->off_out, r->out_bytes);
   if (r->off_plan != Arena::kNone) s->arena.release(r->off_plan, r->plan_dev_bytes);
