@@ -28,22 +28,21 @@ struct LineParam {
   float2 step[8];   // exp(-i 2 pi r delta), r = 0..7
 };
 
+__device__ __forceinline__ float2 phase_at(const LineParam &p, int K);
+
+// m is a power of two, so d / m and the 2^-12 grid split are exact in FP64;
+// the eight steps use the split in FP32 like every other phase (a few FP64
+// operations per line on GB300's narrow FP64 pipe).
 __device__ __forceinline__ void make_param(LineParam &p, double d, int m) {
-  const double delta = d / (double)m;
-  const double dhi = rint(delta * 4096.0) / 4096.0;
+  const double delta = d * (1.0 / (double)m);
+  const double dhi = rint(delta * 4096.0) * (1.0 / 4096.0);
   p.dhi = (float)dhi;
   p.dlo = (float)(delta - dhi);
   const double d2 = d - 2.0 * rint(0.5 * d);   // d mod 2, exact
   p.cnyq = cospif((float)d2);
   p.pad_ = 0.f;
 #pragma unroll
-  for (int r = 0; r < 8; r++) {
-    double t = (double)r * delta;
-    t -= rint(t);
-    float s, c;
-    sincospif(2.0f * (float)t, &s, &c);
-    p.step[r] = make_float2(c, -s);
-  }
+  for (int r = 0; r < 8; r++) p.step[r] = phase_at(p, r);
 }
 
 // exp(-i 2 pi K delta) for integer 0 <= K < 2^11.
