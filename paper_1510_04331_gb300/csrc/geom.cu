@@ -622,8 +622,8 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
 
 // Line pairs (warps) per CTA: 8 for rotation pass 2 (64-byte row pieces of
 // its 16 adjacent scratch columns: 5.05 -> 4.91 ms per survey step; 16
-// pairs 6.23 ms), 4 for the others (shift columns with 8 pairs: 1.88 ->
-// 2.17 ms).  Register budget for 16 resident warps per SM (measured faster
+// pairs 6.23 ms), 4 for the others (with 8 pairs: shift columns 1.88 ->
+// 2.17, shift rows 1.48 -> 1.58, rotation pass 3 1.97 -> 2.04 ms).  Register budget for 16 resident warps per SM (measured faster
 // than 12 for every kind).
 template <int KIND>
 constexpr int w32_ppc() { return KIND == ROT_P2 ? 8 : 4; }
