@@ -1,11 +1,12 @@
 // median.cu -- angle-gated median PSF subtraction (Sect. 3.3) and median
 // collapse (Sect. 3.4) on sm_103a.
 //
-// Both kernels work in the paper's "spatial" data-parallel scheme: a CTA of
-// 8 warps owns 8 consecutive pixels of every frame (one warp per pixel) and
-// reads, per frame, those 8 pixels as one 32-byte sector.  Values are
-// compared as 32-bit IEEE total-order keys (negative: all bits flipped,
-// positive: sign bit set), so selection is exact and bit-reproducible.
+// The kernels work in the paper's "spatial" data-parallel scheme: a CTA
+// owns consecutive pixels of every frame, one warp per pixel (8 for the
+// general median path, whose CTA reads a 32-byte sector per frame; 4 for the
+// collapse, a 16-byte row per frame).  Values are compared as 32-bit IEEE
+// total-order keys (negative: all bits flipped, positive: sign bit set), so
+// selection is exact and bit-reproducible.
 //
 // PSF subtraction.  Frames are visited in angle order s (perm[s] = frame).
 // For frame s the reference set is the sorted positions [0, L_s) u [R_s, T)
@@ -21,8 +22,10 @@
 //      frames entering/leaving the set and walks a pointer to the k-th set
 //      bit (k = (|S| - 1) / 2), the median being that key (or the mean of it
 //      and the next set bit's key, in FP32, for even |S|).
-// Collapse.  Per pixel, radix select (4 passes of 8-bit histograms with
-// warp-aggregated counts) of the lower median, plus the next key for even T.
+// Collapse.  Per pixel, a value-linear histogram over a sampled range
+// locates the two middle ranks, read off a short candidate list
+// (collapse2_kernel); radix selects (8-bit digits) are its exact fallback and
+// the masked (master sky) and long-cube form (collapse_kernel).
 #include <cuda_runtime.h>
 #include <type_traits>
 #include <stdint.h>
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   for (int s = threadIdx.x; s < T; s += 256) perm_s[s] = (uint16_t)__ldg(&a.perm[s]);
   __syncthreads();
   // a 4-pixel group whose annuli all have a band (or no annulus) belongs to
-  // adi_band_kernel, which runs after this kernel
+  // the band path (psf_band.cu), which runs after this kernel
   bool banded[2];
 #pragma unroll
   for (int g = 0; g < 2; g++) {
