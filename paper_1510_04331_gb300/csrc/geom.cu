@@ -620,13 +620,15 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
   fft1024_warp(v, lane, buf, tw);
 }
 
-// Line pairs (warps) per CTA: 8 for rotation pass 2 (64-byte row pieces of
-// its 16 adjacent scratch columns: 5.05 -> 4.91 ms per survey step; 16
-// pairs 6.23 ms), 4 for the others (with 8 pairs: shift columns 1.88 ->
-// 2.17, shift rows 1.48 -> 1.58, rotation pass 3 1.97 -> 2.04 ms).  Register budget for 16 resident warps per SM (measured faster
+// Line pairs (warps) per CTA: 8 for rotation passes 1 and 2 (64-byte row
+// pieces of 16 adjacent columns, and a CTA's warps keep the unrolled
+// transform's code warm together: pass 2 5.05 -> 4.91 ms per survey step,
+// 16 pairs 6.23 ms; pass 1 2.63 -> 2.56 ms), 4 for the others (with 8 pairs:
+// shift columns 1.88 -> 2.17, shift rows 1.48 -> 1.58, rotation pass 3
+// 1.97 -> 2.04 ms).  Register budget for 16 resident warps per SM (measured faster
 // than 12 for every kind).
 template <int KIND>
-constexpr int w32_ppc() { return KIND == ROT_P2 ? 8 : 4; }
+constexpr int w32_ppc() { return (KIND == ROT_P2 || KIND == ROT_P1) ? 8 : 4; }
 constexpr size_t w32_smem_bytes(int ppc) { return (size_t)ppc * (1024 + 1024 / 32) * sizeof(float2); }
 
 template <int KIND>
@@ -725,41 +727,50 @@ __global__ void __launch_bounds__(32 * w32_ppc<KIND>(), 16 / w32_ppc<KIND>()) li
   const bool RCOLS = (KIND == ROT_P1) && (q & 1);
   if (RCOLS) {
     if (q == 1) {
-      constexpr int IT = 2 * N / (32 * PPC);
+      constexpr int IT = HP * N / (32 * PPC);
       float4 q4[IT];
 #pragma unroll
       for (int k = 0; k < IT; k++) {
-        const int i = threadIdx.x + k * 32 * PPC, row = i >> 1, h = i & 1;
+        const int i = threadIdx.x + k * 32 * PPC, row = i / HP, h = i % HP;
         q4[k] = row == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)   // row 0 would be element n
                          : *reinterpret_cast<const float4 *>(fin + (size_t)row * N + col0 + 4 * h);
       }
 #pragma unroll
       for (int k = 0; k < IT; k++) {
-        const int i = threadIdx.x + k * 32 * PPC, row = i >> 1, h = i & 1;
+        const int i = threadIdx.x + k * 32 * PPC, row = i / HP, h = i % HP;
         if (row == 0) continue;
         sbuf[2 * h][pad32(N - row)] = make_float2(q4[k].x, q4[k].y);
         sbuf[2 * h + 1][pad32(N - row)] = make_float2(q4[k].z, q4[k].w);
       }
       if (threadIdx.x < PPC) sbuf[threadIdx.x][pad32(0)] = make_float2(0.f, 0.f);
     } else {
-      const int cb = N - col0 - 8;                     // >= 0, multiple of 8
+      // lines col0 + 2p and col0 + 2p + 1 are frame columns n - col0 - 2p and
+      // n - col0 - 2p - 1: the row's 2 PPC floats from column cb, plus column
+      // n - col0 for line col0 (line 0 of the frame is zero)
+      constexpr int NF = 2 * PPC;
+      const int cb = N - col0 - NF;                    // >= 0, a multiple of NF
       constexpr int IT = N / (32 * PPC);
-      float4 lo4[IT], hi4[IT];
+      float f[IT][NF];
       float top[IT];
 #pragma unroll
       for (int k = 0; k < IT; k++) {
         const float *rowp = fin + (size_t)(threadIdx.x + k * 32 * PPC) * N;
-        lo4[k] = *reinterpret_cast<const float4 *>(rowp + cb);
-        hi4[k] = *reinterpret_cast<const float4 *>(rowp + cb + 4);
-        top[k] = (col0 > 0) ? rowp[N - col0] : 0.f;   // line 0 of the frame is zero
+#pragma unroll
+        for (int u = 0; u < NF / 4; u++) {
+          const float4 x = *reinterpret_cast<const float4 *>(rowp + cb + 4 * u);
+          f[k][4 * u] = x.x;
+          f[k][4 * u + 1] = x.y;
+          f[k][4 * u + 2] = x.z;
+          f[k][4 * u + 3] = x.w;
+        }
+        top[k] = (col0 > 0) ? rowp[N - col0] : 0.f;
       }
 #pragma unroll
       for (int k = 0; k < IT; k++) {
         const int pos = threadIdx.x + k * 32 * PPC;
-        sbuf[0][pad32(pos)] = make_float2(top[k], hi4[k].w);
-        sbuf[1][pad32(pos)] = make_float2(hi4[k].z, hi4[k].y);
-        sbuf[2][pad32(pos)] = make_float2(hi4[k].x, lo4[k].w);
-        sbuf[3][pad32(pos)] = make_float2(lo4[k].z, lo4[k].y);
+#pragma unroll
+        for (int pp = 0; pp < PPC; pp++)
+          sbuf[pp][pad32(pos)] = make_float2(pp == 0 ? top[k] : f[k][NF - 2 * pp], f[k][NF - 1 - 2 * pp]);
       }
     }
     __syncthreads();

@@ -100,15 +100,15 @@ def test_rotate_matches_oracle(g, n):
 
 @pytest.mark.parametrize("n", [512, 1024])
 def test_rotate_matches_oracle_large(g, n):
-    th = [37.7, -101.2]
-    f = synth.random_frames(2, n, seed=n + 2)
+    th = [37.7, -101.2, 100.4, 171.9, -178.0]     # quarter turns q = 0, 3, 1, 2, 2
+    f = synth.random_frames(len(th), n, seed=n + 2)
     out = g.graphic_rotate(dev(f), th)
     ref = oracle.rotate(f.astype(np.float64), th)
     assert rel_err(out, ref, np.abs(f).max()) <= TOL
 
 
-def test_rotate_quarter_turns_exact(g):
-    n = 64
+@pytest.mark.parametrize("n", [64, 512])
+def test_rotate_quarter_turns_exact(g, n):
     f = synth.random_frames(5, n, seed=3)
     th = [0.0, 90.0, 180.0, 270.0, -90.0]
     out = g.graphic_rotate(dev(f), th).cpu().numpy()
