@@ -565,54 +565,71 @@ __device__ __forceinline__ void w32_filter(float2 (&v)[32], int lane, float2 *bu
   fft1024_warp<KIND != ROT_P3>(v, lane, buf, tw);   // only rotation pass 3 reads whole 1024-point lines
 
   // ---- middle: v[r] = Z_k, k = lane + 32 r --------------------------------
-  if constexpr (!SAME_D) {
-#pragma unroll
-    for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
-    __syncwarp();
-  }
   // the 1/m of the inverse and the 1/2 of the pair separation are powers of
   // two, carried by the phasors (the same bits as scaling each product)
   constexpr float sc = SAME_D ? 1.0f / (float)M : 0.5f / (float)M;
-  // phasors H_k = exp(-i 2 pi ks delta), ks the signed bin: exact anchors at
-  // r = 0, 8, 16, 24, a product with exp(-i 2 pi 32 delta) in between
   const float2 sa = phase_at(la, 32);
-  const float2 sb = SAME_D ? sa : phase_at(lb, 32);
-  float2 ha, hb;
+  if constexpr (SAME_D) {
+    // one shift for both lines: V_k = Z_k H_k, H_k = exp(-i 2 pi ks delta),
+    // ks the signed bin: exact anchors at r = 0, 8, 16, 24, a product with
+    // exp(-i 2 pi 32 delta) in between
+    float2 ha;
 #pragma unroll
-  for (int r = 0; r < 32; r++) {
-    const int k = lane + 32 * r;
-    if ((r & 7) == 0) {
-      const int ks = (r < 16) ? k : k - M;
-      const float2 pa = phase_at(la, ks);
-      ha = make_float2(pa.x * sc, pa.y * sc);
-      if constexpr (SAME_D) {
-        hb = ha;
+    for (int r = 0; r < 32; r++) {
+      const int k = lane + 32 * r;
+      if ((r & 7) == 0) {
+        const float2 pa = phase_at(la, (r < 16) ? k : k - M);
+        ha = make_float2(pa.x * sc, pa.y * sc);
       } else {
-        const float2 pb = phase_at(lb, ks);
-        hb = make_float2(pb.x * sc, pb.y * sc);
+        ha = cmul(ha, sa);
       }
-    } else {
-      ha = cmul(ha, sa);
-      hb = SAME_D ? ha : cmul(hb, sb);
+      const float2 ua = (r == 16 && lane == 0) ? make_float2(la.cnyq * sc, 0.f) : ha;   // Nyquist bin
+      const float2 vk = cmul(v[r], ua);
+      v[r] = make_float2(vk.x, -vk.y);   // conj(V) / m
     }
-    float2 ua = ha, ub = hb;
-    if (r == 16 && lane == 0) {   // Nyquist bin
-      ua = make_float2(la.cnyq * sc, 0.f);
-      ub = make_float2(lb.cnyq * sc, 0.f);
-    }
-    const float2 z = v[r];
-    float2 vk;
-    if constexpr (SAME_D) {
-      vk = cmul(z, ua);
-    } else {
-      // twice the spectra of lines a and b
-      const float2 zm = buf[pad32((M - k) & (M - 1))];
+  } else {
+    // lines a and b shifted by their own amounts.  Bins k and M - k share the
+    // separated spectra (A_{M-k} = conj A_k, B_{M-k} = conj B_k) and the
+    // phasors (H_{-k} = conj H_k), so each lane computes its bins k < M/2
+    // (r < 16) and hands V_{M-k} to the lane that holds bin M - k; lane 0
+    // computes its own bins 0 and M/2 (each its own partner).
+#pragma unroll
+    for (int r = 0; r < 32; r++) buf[pad32(lane + 32 * r)] = v[r];
+    __syncwarp();
+    const float2 sb = phase_at(lb, 32);
+    float2 ha, hb;
+#pragma unroll
+    for (int r = 0; r < 16; r++) {
+      const int k = lane + 32 * r;
+      if ((r & 7) == 0) {
+        const float2 pa = phase_at(la, k), pb = phase_at(lb, k);
+        ha = make_float2(pa.x * sc, pa.y * sc);
+        hb = make_float2(pb.x * sc, pb.y * sc);
+      } else {
+        ha = cmul(ha, sa);
+        hb = cmul(hb, sb);
+      }
+      // twice the spectra of lines a and b; location M - k is read and
+      // written by this lane only
+      const int jm = pad32((M - k) & (M - 1));
+      const float2 z = v[r], zm = buf[jm];
       const float2 A = make_float2(z.x + zm.x, z.y - zm.y);
       const float2 B = make_float2(z.y + zm.y, zm.x - z.x);
-      const float2 P = cmul(A, ua), Q = cmul(B, ub);
-      vk = make_float2(P.x - Q.y, P.y + Q.x);
+      const float2 P = cmul(A, ha), Q = cmul(B, hb);
+      v[r] = make_float2(P.x - Q.y, -(P.y + Q.x));                 // conj(V_k) / m
+      if (r > 0 || lane > 0) buf[jm] = make_float2(P.x + Q.y, P.y - Q.x);   // conj(V_{M-k}) / m
     }
-    v[r] = make_float2(vk.x, -vk.y);   // conj(V) / m
+    if (lane == 0) {   // Nyquist bin M/2: v[16] holds it, its own partner
+      const float2 z = v[16];
+      const float2 A = make_float2(z.x + z.x, z.y - z.y);
+      const float2 B = make_float2(z.y + z.y, z.x - z.x);
+      const float2 P = cmul(A, make_float2(la.cnyq * sc, 0.f)), Q = cmul(B, make_float2(lb.cnyq * sc, 0.f));
+      v[16] = make_float2(P.x - Q.y, -(P.y + Q.x));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 16; r < 32; r++)
+      if (r > 16 || lane > 0) v[r] = buf[pad32(lane + 32 * r)];
   }
   __syncwarp();
 
