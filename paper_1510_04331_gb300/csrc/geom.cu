@@ -356,9 +356,17 @@ __device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, i
     const LineParam &la = lp[SAME_D ? 0 : 2 * p];
     const LineParam &lb = lp[SAME_D ? 0 : 2 * p + 1];
     const float inv_m = 1.0f / (float)M;
+    // the 1/m of the inverse (and the 1/2 of the separation) are powers of
+    // two, carried by the phasor base (the same bits as scaling each product)
+    constexpr float sc = SAME_D ? 1.0f / (float)M : 0.5f / (float)M;
     const int K0 = 8 * j;
-    const float2 ba = phase_at(la, K0);
-    const float2 bb = SAME_D ? ba : phase_at(lb, K0);
+    const float2 pa0 = phase_at(la, K0);
+    const float2 ba = make_float2(pa0.x * sc, pa0.y * sc);
+    float2 bb = ba;
+    if constexpr (!SAME_D) {
+      const float2 pb0 = phase_at(lb, K0);
+      bb = make_float2(pb0.x * sc, pb0.y * sc);
+    }
 #pragma unroll
     for (int r = 0; r < 8; r++) {
       const int k = K0 + r;
@@ -375,15 +383,15 @@ __device__ __forceinline__ void line_pass_body(const LineArgs &a, long long f, i
         vm = cmul(zm, cconj(ha));
       } else {
         const float2 hb = cmul(bb, lb.step[r]);
-        // A = (Z_k + conj Z_{-k}) / 2,  B = (Z_k - conj Z_{-k}) / (2i)
-        const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-        const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+        // 2A = Z_k + conj Z_{-k},  2B = (Z_k - conj Z_{-k}) / i
+        const float2 A = make_float2(z.x + zm.x, z.y - zm.y);
+        const float2 B = make_float2(z.y + zm.y, zm.x - z.x);
         const float2 P = cmul(A, ha), Q = cmul(B, hb);
         vk = make_float2(P.x - Q.y, P.y + Q.x);     // P + i Q
         vm = make_float2(P.x + Q.y, Q.x - P.y);     // conj P + i conj Q
       }
-      spec[padi(k)] = make_float2(vk.x * inv_m, -vk.y * inv_m);
-      spec[padi(M - k)] = make_float2(vm.x * inv_m, -vm.y * inv_m);
+      spec[padi(k)] = make_float2(vk.x, -vk.y);
+      spec[padi(M - k)] = make_float2(vm.x, -vm.y);
     }
     if (j == 0) {
       float2 z = spec[padi(M / 2)];
