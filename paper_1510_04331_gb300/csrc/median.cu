@@ -450,7 +450,6 @@ __global__ void __launch_bounds__(256, 1) adi_median_kernel(const AdiArgs a, int
   __shared__ int ann_s[8];
 
   const int T = a.T;
-  const long long NN = (long long)a.n * a.n;
   const long long p0 = (long long)(a.gen_list ? __ldg(&a.groups[a.gen_off + blockIdx.x]) : (int)blockIdx.x) * 8;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = tcap / 32;   // bitmap words per lane column
