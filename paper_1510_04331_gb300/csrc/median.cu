@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
     const unsigned lt = (1u << lane) - 1u;
     int len = 0;
     // four 32-frame rounds per step: their loads and bins are independent;
-    // the list holds total-order keys
+    // the list holds total-order keys.  Bins bin0 .. bin1 of x >= 0 are the
+    // x in [bin0, bin1 + 1) (truncation is the floor there; -0 is in bin 0).
+    const float xlo = (float)bin[0], xhi = (float)(bin[1] + 1);
     for (int t0 = 0; t0 < T; t0 += 128) {
       float v[4];
       bool in[4];
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseA
         const int t = t0 + 32 * u + lane;
         v[u] = t < T ? __uint_as_float(kw[t * C2_KS]) : 0.f;
         const float xv = (v[u] - lo) * scale;
-        in[u] = t < T && xv >= 0.f && xv < 256.f && (unsigned)((int)xv - bin[0]) <= (unsigned)(bin[1] - bin[0]);
+        in[u] = t < T && xv >= xlo && xv < xhi;
       }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
