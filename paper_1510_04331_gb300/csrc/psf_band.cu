@@ -803,8 +803,22 @@ cudaError_t launch_adi_band(const AdiArgs &a, cudaStream_t st, int *launched) {
     b.nwt = nwt;
     b.slot_bytes = Slot(b.NB, nwt).bytes;
     // candidates: the band (more than NB / 2 ranks) and the spill of its two
-    // end bins (a few dozen keys), at most T
+    // end bins (a few dozen keys), at most T; then as many more as fit the
+    // shared memory without costing a resident CTA (a pixel whose located
+    // bins hold more takes the exact path)
     b.cap = std::min(T, b.NB + std::max(64, b.NB / 4));
+    {
+      int dev = 0, per_sm = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+          per_sm > 0) {
+        const size_t reserve = 1024;   // per resident CTA
+        auto ctas = [&](int c) { return (size_t)per_sm / (prep_smem_bytes(T, c, nwt) + reserve); };
+        const size_t occ = ctas(b.cap);
+        while (b.cap + 32 <= T && ctas(b.cap + 32) == occ && prep_smem_bytes(T, b.cap + 32, nwt) <= 227 * 1024)
+          b.cap += 32;
+      }
+    }
     const size_t psmem = prep_smem_bytes(T, b.cap, nwt);
     cudaError_t e = cudaFuncSetAttribute(band_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
