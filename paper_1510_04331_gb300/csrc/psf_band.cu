@@ -416,7 +416,8 @@ __global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
 
 // Shared memory: per warp skeys[NB] u32, blev[NB] u32, bm[NB] u32 (bit map,
 // word wd of lane c at wd * 32 + c), blpos[NB] u16, belowc[nwt + 1] uint2
-// (BELOW word, BELOW frames before it); per CTA the value / residual blocks.
+// (BELOW word, BELOW frames before it); per CTA three value blocks (each
+// replaced by its residuals in place).
 // The gates (L_i, R_i) are read through L1 (a few KB per annulus, shared by
 // every CTA of the annulus): measured faster than staging them, which cost
 // resident CTAs.
@@ -444,8 +445,9 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   uint16_t *blpos = reinterpret_cast<uint16_t *>(bm + NB);
   uint2 *belowc = reinterpret_cast<uint2 *>(wb + (size_t)NB * 12 + al16((size_t)NB * 2));
   unsigned char *cb_ = ssm + PPC * sweep_warp_bytes(NB, nwt);
-  float4 *vbuf = reinterpret_cast<float4 *>(cb_);                                      // [2][SWK][32]
-  float *obuf = reinterpret_cast<float *>(cb_ + 2 * kBlockBytes);                       // [SWK][32][4]
+  // [3][SWK][32] 16-byte rows: block b's values in buffer b % 3, replaced by
+  // its residuals in place (each slot is read, then written, by one thread)
+  float4 *vbuf = reinterpret_cast<float4 *>(cb_);
 
   // ---- this pixel's band data -------------------------------------------
   const char *slot = B.slots + ((size_t)blockIdx.x * PPC + w) * B.slot_bytes;
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   const int i1 = min(T, i0 + C);
   const int nblk = (C + SWK - 1) / SWK;
   auto prefetch = [&](int b) {
-    float4 *dst = vbuf + (b & 1) * SWK * 32;
+    float4 *dst = vbuf + (b % 3) * SWK * 32;
     for (int q = threadIdx.x; q < SWK * 32; q += 32 * PPC) {
       const int kk = q >> 5, cc = q & 31;
       const int i = cc * C + b * SWK + kk;
@@ -556,15 +558,24 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
   int2 gnext = lane_ok ? __ldg(&gate_g[i0]) : make_int2(0, 0);
 
   // ---- sweep ------------------------------------------------------------
-  for (int b = 0; b < nblk; b++) {
-    if (b + 1 < nblk) {
-      prefetch(b + 1);
-      cp_async_wait_group<1>();
-    } else {
-      cp_async_wait_group<0>();
+  // one barrier per block: after it block b's values are in and block b-1's
+  // residuals are complete; block b+1's copies go to the third buffer, and
+  // block b-1's residuals are written out while block b is swept
+  auto store_block = [&](int bb) {
+    const float4 *ob = vbuf + (bb % 3) * SWK * 32;
+    for (int q = threadIdx.x; q < SWK * 32; q += 32 * PPC) {
+      const int kk = q >> 5, cc = q & 31;
+      const int i = cc * C + bb * SWK + kk;
+      if (bb * SWK + kk < C && i < T)
+        *reinterpret_cast<float4 *>(a.out + (long long)(a.perm_id ? i : __ldg(&a.perm[i])) * a.out_fs + p0) = ob[q];
     }
-    __syncthreads();   // block b's values are in; block b-1's residuals are written out
-    const float4 *vb = vbuf + (b & 1) * SWK * 32;
+  };
+  for (int b = 0; b < nblk; b++) {
+    cp_async_wait_group<0>();
+    __syncthreads();
+    if (b + 1 < nblk) prefetch(b + 1);
+    if (b > 0) store_block(b - 1);
+    float *vb = reinterpret_cast<float *>(vbuf + (b % 3) * SWK * 32);
     for (int kk = 0; kk < SWK; kk++) {
       const int i = i0 + b * SWK + kk;
       if (b * SWK + kk >= C || i >= i1) break;
@@ -630,24 +641,17 @@ __global__ void __launch_bounds__(32 * PPC, (WC <= 8) ? 9 : (WC == 16 ? 4 : 2)) 
             if (rest) med = (med + hi) * 0.5f;
             else fail = true;
           }
-          res = reinterpret_cast<const float *>(vb)[(kk * 32 + c) * 4 + w] - med;
+          res = vb[(kk * 32 + c) * 4 + w] - med;
         } else {
           fail = true;
         }
         if (fail) lane_ok = false;
       }
-      obuf[(kk * 32 + c) * 4 + w] = res;
-    }
-    __syncthreads();   // block b's residuals are complete
-    for (int q = threadIdx.x; q < SWK * 32; q += 32 * PPC) {
-      const int kk = q >> 5, cc = q & 31;
-      const int i = cc * C + b * SWK + kk;
-      if (b * SWK + kk < C && i < T) {
-        const float4 r4 = reinterpret_cast<const float4 *>(obuf)[q];
-        *reinterpret_cast<float4 *>(a.out + (long long)(a.perm_id ? i : __ldg(&a.perm[i])) * a.out_fs + p0) = r4;
-      }
+      vb[(kk * 32 + c) * 4 + w] = res;
     }
   }
+  __syncthreads();   // the last block's residuals are complete
+  if (nblk > 0) store_block(nblk - 1);
   if (ann >= 0 && (hdr.w != 1 || nb > NB)) fail = true;
   if (__any_sync(FULL, fail) && lane == 0) atomicOr(a.status, STATUS_INTERNAL);
 }
