@@ -121,7 +121,7 @@ def job_throughput(units_per_rank_step, steps, world, max_ms):
 # (bytes per step at that size, source).  Per launch = bytes / launches.
 MEASURED_TRAFFIC = {
     ("adi_band_sweep", 2000, 512): (
-        5.7650e9,
+        5.8944e9,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the five band-sweep launches of one median step on "
         "the 2000x512^2 survey cube itself (profiles/band_sweep_kernel_survey_2000x512.md)"),
 }
