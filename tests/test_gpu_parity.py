@@ -251,6 +251,16 @@ def test_reduce_host_equals_device_path(g):
     assert np.array_equal(a, b)
 
 
+def test_reduce_host_pieces_equal_device_path(g):
+    """300 frames of 512 x 512 (300 MB): the host-buffer path copies and
+    shifts the cube in two pieces; the result is the device path's, bit for
+    bit."""
+    d = synth.make_cube(300, 512, seed=5, parang=synth.altaz_parang(300), edges=synth.default_edges(512))
+    a = g.graphic_reduce(dev(d.cube), d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges).cpu().numpy()
+    b = g.graphic_reduce_host(d.cube, d.dx, d.dy, d.parang, d.fwhm, d.n_fwhm, d.edges)
+    assert np.array_equal(a, b)
+
+
 @pytest.fixture(scope="module")
 def survey():
     return synth.survey_cube(seed=1)
