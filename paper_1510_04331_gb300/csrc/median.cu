@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(32 * COL_PPC) collapse_kernel(const CollapseAr
 // range, a list longer than 256 keys (many equal values) or a non-finite
 // value falls back to exact radix selects of the two middle ranks over all
 // keys.
-__global__ void __launch_bounds__(32 * COL_PPC) collapse2_kernel(const CollapseArgs a) {
+__global__ void __launch_bounds__(32 * COL_PPC, 5) collapse2_kernel(const CollapseArgs a) {
   extern __shared__ uint32_t csm[];
   uint32_t *hist_all = csm;                       // [COL_PPC][512]
   uint32_t *keys_all = csm + COL_PPC * 512;       // [T][C2_KS]

@@ -172,7 +172,7 @@ __host__ __device__ inline size_t prep_smem_bytes(int T, int cap, int nwt) {
   return al16((size_t)T * KS * 4) + PPC * prep_warp_bytes(cap, nwt);
 }
 
-__global__ void __launch_bounds__(32 * PPC) band_prep_kernel(const BandArgs B) {
+__global__ void __launch_bounds__(32 * PPC, 4) band_prep_kernel(const BandArgs B) {
   extern __shared__ __align__(16) unsigned char psm[];
   const AdiArgs &a = B.a;
   const int T = a.T;
